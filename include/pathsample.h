@@ -1,0 +1,214 @@
+/*
+ * pathsample.h -- C interface of the GPU path-sampling library.
+ *
+ * The library estimates the counts of all six connected induced 4-vertex
+ * subgraphs of an undirected simple graph by 3-path sampling and centred
+ * 3-path sampling (Jha, Seshadhri & Pinar, "Path Sampling: A Fast and
+ * Provable Method for Estimating 4-Vertex Subgraph Counts").  Every step of
+ * the sampling path runs in CUDA kernels for sm_103a (GB300).
+ *
+ * Motif numbering (the matrix of Eq. (1)): 1 = 3-star, 2 = 3-path,
+ * 3 = tailed triangle, 4 = 4-cycle, 5 = chordal 4-cycle, 6 = 4-clique.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers; all others are host pointers.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    queued on it; only the calls documented as synchronising wait for it.
+ *  - The library never allocates device memory: all of it lives in the
+ *    caller's workspace (see ps_graph_workspace_bytes).
+ *  - Every call returns a status code (below); none throws, none traps the
+ *    GPU.  Device-side faults in the input are reported through status codes.
+ *  - Random draws are a pure function of (seed, sample id), so a range of
+ *    sample ids gives the same class counts however it is split over calls,
+ *    streams, launches or GPUs.
+ */
+#ifndef PATHSAMPLE_H
+#define PATHSAMPLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ps_stream_t; /* same type as cudaStream_t */
+
+/* ---------------------------------------------------------------- status */
+#define PS_OK 0
+#define PS_NO_PATHS 1          /* W == 0 or Lambda == 0: nothing to sample      */
+#define PS_ERR_ARG (-1)        /* bad argument, malformed offsets, column range */
+#define PS_ERR_NOT_SIMPLE (-2) /* self-loop or repeated neighbour                */
+#define PS_ERR_ASYMMETRIC (-3) /* an arc without its reverse                     */
+#define PS_ERR_WORKSPACE (-4)  /* workspace missing, too small or misaligned     */
+#define PS_ERR_OVERFLOW (-5)   /* W or Lambda does not fit in 64 bits            */
+#define PS_ERR_TIMEOUT (-6)    /* a bounded device wait expired                  */
+#define PS_ERR_CUDA (-7)       /* a CUDA runtime call failed                     */
+#define PS_ERR_STATE (-8)      /* call out of order (e.g. sampling before prefix) */
+#define PS_ERR_NOMEM (-9)      /* host allocation failed                         */
+
+/* Tuning knobs.  None of them changes any result; they only change speed.
+ * Pass NULL for the defaults; a zero field also means "default". */
+typedef struct {
+    int32_t block_size;         /* sampling threads per block: 128, 256 (default), 512, 1024 */
+    int32_t blocks_per_sm;      /* resident sampling blocks per SM (default: occupancy)      */
+    int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1); -1 = none  */
+    int32_t hub_count;          /* top-degree vertices given an adjacency bitmap row
+                                   (default: up to 1024 rows within 256 MB); -1 = none      */
+    int32_t samples_per_thread; /* reserved (1)                                             */
+    int32_t reserved[3];
+} ps_tuning;
+
+/* Totals of one graph, filled by ps_tau_prefix. */
+typedef struct {
+    uint64_t W;       /* sum over edges of tau_e = (d_u - 1)(d_v - 1), Section 3       */
+    uint64_t Lambda;  /* sum over edges of lambda_e = L_{u,v} L_{v,u}, Section 4        */
+    uint64_t N1_lo;   /* N_1 = sum_v C(d_v, 3) (3-stars, Alg. 2) as a 128-bit integer  */
+    uint64_t N1_hi;
+    int64_t n;        /* vertices                                                        */
+    int64_t m;        /* undirected edges                                                */
+    int64_t d_max;    /* largest degree                                                  */
+    int64_t hubs;     /* vertices with a bitmap row                                      */
+    int32_t tau_shift;    /* guide bucket of r is r >> shift (tau prefix)               */
+    int32_t lambda_shift; /* same for the lambda prefix                                  */
+} ps_stats;
+
+typedef struct ps_graph ps_graph; /* opaque; host metadata + pointers into the workspace */
+
+/* Bytes of device workspace a graph with n vertices and nnz stored arcs
+ * (nnz = 2m) needs under tuning t (NULL = defaults).  0 if the sizes are
+ * outside the supported range (n < 2^31, nnz < 2^31). */
+size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
+
+/* Section 2 input and Section 4 order.  Reads the CSR graph (d_off: int64
+ * [n + 1], d_col: int32 [nnz]; rows in any order, both arc directions
+ * stored), checks that it is an undirected simple graph, relabels every
+ * vertex by its rank in the order "d_u < d_v, ties by smaller id" (so the
+ * order becomes integer order), rebuilds the adjacency lists sorted
+ * ascending, and builds the edge table (u < v, u ascending then v ascending)
+ * with the positions of each edge in both endpoint lists.
+ *
+ * d_off / d_col belong to the caller and are only read during the call.
+ * d_workspace (ws_bytes >= ps_graph_workspace_bytes(n, nnz, t), 256-byte
+ * aligned) must stay allocated and untouched until ps_graph_free(*out).
+ * Synchronises `stream` (to read the validation flags).  On error *out is
+ * NULL and the status is PS_ERR_ARG / PS_ERR_NOT_SIMPLE / PS_ERR_ASYMMETRIC
+ * (highest-priority first) or PS_ERR_WORKSPACE / PS_ERR_CUDA. */
+int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_col,
+                void *d_workspace, size_t ws_bytes, const ps_tuning *t, ps_stream_t stream,
+                ps_graph **out);
+
+/* Section 3 (tau_e, W) and Section 4 (lambda_e, Lambda), the edge
+ * distributions of Alg. 1 and Alg. 3: computes both weights of every edge, their inclusive uint64 prefix
+ * sums (exact, so the edge draw is exact), N_1 of Alg. 2, the guide tables
+ * of the inverse-CDF search and the hub adjacency bitmap.  Synchronises
+ * `stream` and fills *out.  Returns PS_NO_PATHS when W == 0 or Lambda == 0
+ * (sampling then leaves histograms untouched), PS_ERR_OVERFLOW when a sum
+ * does not fit in 64 bits, PS_ERR_TIMEOUT when the scan's bounded wait
+ * expired. */
+int ps_tau_prefix(ps_graph *g, ps_stream_t stream, ps_stats *out);
+
+/* Alg. 1 run k times, counted as in Alg. 2: sample ids first_id ..
+ * first_id + k - 1, seed `seed`.  ADDS the class counts to d_hist6 (device,
+ * uint64 [6]: triangle (u' == v', no motif), 3-path, tailed triangle,
+ * 4-cycle, chordal 4-cycle, 4-clique).  Asynchronous on `stream`.  Returns
+ * PS_NO_PATHS (and adds nothing) when W == 0. */
+int ps_sample_3paths(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
+                     uint64_t *d_hist6, ps_stream_t stream);
+
+/* Alg. 3 run k times, counted as in Alg. 4.  ADDS to d_hist4 (device,
+ * uint64 [4]: not centred, 4-cycle, chordal 4-cycle, 4-clique).
+ * Asynchronous.  Returns PS_NO_PATHS (adds nothing) when Lambda == 0. */
+int ps_sample_centered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
+                       uint64_t *d_hist4, ps_stream_t stream);
+
+/* The estimators of Alg. 2 and Alg. 4 and the final combination of
+ * Section 4 (C1..C3 from the 3-path counts, C4..C6 from the centred counts;
+ * C1 = N_1 - C3 - 2 C5 - 4 C6 with the 3-path sampler's terms), plus the
+ * error bars of Corollary 5.3 at confidence 1 - delta (the C1 bar adds those
+ * of C3, 2 C5 and 4 C6).  Pure host function (FP64): hist6 / hist4 are host
+ * copies of the histograms, k3 / kc their sample counts.  est, lo, hi
+ * receive 6 values each, indexed by motif - 1.  Returns PS_ERR_ARG for
+ * k3 == 0, kc == 0 or delta outside (0, 1); PS_NO_PATHS when W or Lambda is
+ * 0 (the estimates are then exact: no 3-path / no 4-cycle exists). */
+int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
+                const uint64_t hist4[4], uint64_t kc, double delta, double est[6],
+                double lo[6], double hi[6]);
+
+/* Releases the host metadata of g (not the workspace, which the caller owns). */
+void ps_graph_free(ps_graph *g);
+
+/* Short description of a status code (static string). */
+const char *ps_strerror(int code);
+
+/* Which array ps_graph_copy copies out. */
+#define PS_ARRAY_OFFSETS 0 /* int64 [n + 1]   canonical row offsets                      */
+#define PS_ARRAY_COLUMNS 1 /* int32 [nnz]     canonical sorted adjacency                 */
+#define PS_ARRAY_RANK 2    /* int32 [n]       canonical label of each input vertex       */
+#define PS_ARRAY_EDGES 3   /* int32 [m][8]    u, v, d_u, d_v, iu, jv, off_u, off_v       */
+#define PS_ARRAY_PTAU 4    /* uint64 [m]      inclusive prefix of tau                    */
+#define PS_ARRAY_PLAMBDA 5 /* uint64 [m]      inclusive prefix of lambda                 */
+
+/* Copies one device array of g into dst (host or device memory, `bytes` =
+ * exactly the array's size) and synchronises `stream`.  For inspection and
+ * tests. */
+int ps_graph_copy(const ps_graph *g, int which, void *dst, size_t bytes, ps_stream_t stream);
+
+/* ------------------------------------------------------------ end to end */
+
+/* The whole path for one graph held in HOST memory (pinned for speed):
+ * copies the CSR to the device, runs ps_load_csr, ps_tau_prefix, k3 3-path
+ * and kc centred samples (seed, ids from 0), copies the histograms back and
+ * fills est / lo / hi as ps_estimate.  hist6 / hist4 (host, may be NULL)
+ * receive the class counts.  d_workspace must hold
+ * ps_end_to_end_workspace_bytes(n, nnz, t) bytes.  Synchronises `stream`. */
+size_t ps_end_to_end_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
+int ps_count_motifs_host(int64_t n, int64_t nnz, const int64_t *h_off, const int32_t *h_col,
+                         uint64_t k3, uint64_t kc, uint64_t seed, double delta,
+                         void *d_workspace, size_t ws_bytes, const ps_tuning *t,
+                         ps_stream_t stream, uint64_t hist6[6], uint64_t hist4[4],
+                         ps_stats *stats, double est[6], double lo[6], double hi[6]);
+
+/* --------------------------------------------------------------- batched */
+
+/* One unit of batched work: sample ids [first_id, first_id + count) of
+ * graph `graph` (index into the table given to ps_batch_sample) with seed
+ * `seed`, sampler 0 = Alg. 1 (adds into d_hist + 6 * slot), 1 = Alg. 3
+ * (adds into d_hist + 6 * slot, first 4 words).  32 bytes. */
+typedef struct {
+    uint64_t first_id;
+    uint64_t seed;
+    uint32_t count;
+    uint32_t graph;
+    uint32_t slot;
+    uint32_t sampler;
+} ps_work;
+
+/* Runs many work items, over many loaded graphs, in one persistent launch:
+ * blocks take items from a device-side queue.  graphs: host array of
+ * n_graphs handles (each after ps_tau_prefix); d_items: device array of
+ * n_items ps_work; d_hist: device uint64 [6 * slots] (added to); d_table:
+ * device scratch of ps_batch_table_bytes(n_graphs) bytes (graph descriptors,
+ * written by this call); d_counter: device uint32 scratch (zeroed by this
+ * call).  Each item's counts equal those of the corresponding plain call.
+ * Asynchronous. */
+size_t ps_batch_table_bytes(int32_t n_graphs);
+int ps_batch_sample(const ps_graph *const *graphs, int32_t n_graphs, const ps_work *d_items,
+                    int64_t n_items, uint64_t *d_hist, void *d_table, uint32_t *d_counter,
+                    const ps_tuning *t, ps_stream_t stream);
+
+/* Writes the graph descriptors for ps_batch_sample_prepared into d_table
+ * (d_table: device, ps_batch_table_bytes(n_graphs) bytes).  Synchronises
+ * `stream`.  The graphs must stay loaded while the table is used. */
+int ps_batch_prepare(const ps_graph *const *graphs, int32_t n_graphs, void *d_table,
+                     ps_stream_t stream);
+/* Same as ps_batch_sample with a table already written by ps_batch_prepare
+ * (for capture in CUDA graphs: no host-to-device copy inside). */
+int ps_batch_sample_prepared(const void *d_table, int32_t n_graphs, const ps_work *d_items,
+                             int64_t n_items, uint64_t *d_hist, uint32_t *d_counter,
+                             const ps_tuning *t, ps_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PATHSAMPLE_H */

@@ -280,7 +280,7 @@ uint32_t or_draw_small(uint64_t seed, uint64_t id, uint32_t stream, uint32_t slo
     }
 }
 
-/* Alg. 1 step 2 / Alg. 3 step 2: the first j with P[j] > r (reading R4) */
+/* The edge draw of Alg. 1 / Alg. 3: the first j with P[j] > r (reading R4) */
 int64_t or_upper_bound(const uint64_t *P, int64_t m, uint64_t r) {
     int64_t lo = 0, hi = m; /* answer in [lo, hi] */
     while (lo < hi) {
@@ -339,7 +339,7 @@ int or_classify_centered(const or_graph *g, int64_t j, uint32_t a, uint32_t b) {
     return 1 + adj(g->off, g->col, up, v) + adj(g->off, g->col, u, vp);
 }
 
-/* Alg. 2, steps 1-5: k runs of Alg. 1 (sample ids first_id .. first_id+k-1)
+/* The sampling loop of Alg. 2: k runs of Alg. 1 (sample ids first_id .. first_id+k-1)
  * and the class counts.  hist6 is added to. */
 void or_sample_3paths(const or_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
                       uint64_t hist6[6]) {
@@ -357,7 +357,7 @@ void or_sample_3paths(const or_graph *g, uint64_t k, uint64_t seed, uint64_t fir
     }
 }
 
-/* Alg. 4, steps 1-6: k runs of Alg. 3 and the counts of centred outputs. */
+/* The sampling loop of Alg. 4: k runs of Alg. 3 and the counts of centred outputs. */
 void or_sample_centered(const or_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
                         uint64_t hist4[4]) {
     if (g->Lambda == 0) return;
@@ -472,7 +472,7 @@ void or_chernoff_bounds(uint64_t count, uint64_t k, double delta, double *pl, do
     *pu = 0.5 * (lo + hi);
 }
 
-/* Alg. 2 steps 6-9, Alg. 4 steps 7-8 and the final combination (R10), with
+/* The estimators of Alg. 2 and Alg. 4 and the final combination (R10), with
  * the error bars of Section 5 (R11).  est/lo/hi are indexed by motif - 1.
  * W == 0: no 3-path exists, so C2..C6 = 0 and C1 = N1 exactly; Lambda == 0:
  * no 4-cycle exists, so C4..C6 = 0. */

@@ -1,0 +1,96 @@
+// ps_internal.h -- host-side internals shared by the library's translation
+// units: the graph handle, the workspace layout and error helpers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pathsample.h"
+#include "ps_device.cuh"
+
+namespace ps {
+
+// Sort tiers of the row relabel-and-sort step, by row length.
+constexpr int kTierA = 32;      // one warp, registers
+constexpr int kTierB = 1024;    // one warp, shared memory
+constexpr int kTierC = 32768;   // one block, shared memory (128 KB)
+// Hub rows are only worth a bitmap above this degree.
+constexpr int kHubMinDegree = 64;
+// Items per tile of every scan.
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;
+constexpr int64_t kScanTile = kScanBlock * kScanItems;
+// Rank sort (LSD radix, 8-bit digits).
+constexpr int kRadixBlock = 256;
+constexpr int kRadixItems = 16;
+constexpr int64_t kRadixTile = kRadixBlock * kRadixItems;
+
+struct Tuning {
+    int block_size;
+    int blocks_per_sm;
+    int guide_log2_ratio;  // -1: no guide
+    int hub_count;         // 0: none
+    int samples_per_thread;
+};
+Tuning resolve_tuning(const ps_tuning *t, int64_t n);
+
+struct Layout {
+    int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
+    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub;
+    size_t keys0, keys1, vals0, vals1, rcounts, scan_flag, scan_agg, scan_inc;
+    size_t total;
+};
+bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L);
+
+}  // namespace ps
+
+struct ps_graph {
+    ps::Layout L;
+    ps::Tuning tune;
+    char *ws;
+    int device;
+    int sm_count;
+    int64_t n, nnz, m, d_max;
+    // device arrays (inside ws)
+    ps::u64 *status;
+    int64_t *off;
+    int32_t *col;
+    int32_t *rank;
+    int32_t *lowcnt;
+    int64_t *ubase;
+    int32_t *dnew;
+    ps::EdgeRec *rec;
+    uint64_t *ptau, *plam;
+    int32_t *gtau, *glam;
+    uint32_t *hub;
+    bool prefixed;
+    ps_stats stats;
+    ps::GraphDev dev;
+};
+
+namespace ps {
+
+#define PS_CUDA_TRY(call)                         \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return PS_ERR_CUDA; \
+    } while (0)
+
+int sm_count_of_current_device();
+int flags_to_status(uint64_t flags);
+
+// scan helpers (ps_load.cu)
+template <typename T>
+ScanState<T> scan_state(ps_graph *g, int counter_slot);
+int reset_scan(ps_graph *g, int counter_slot, int64_t count, cudaStream_t s);
+
+// steps (one translation unit each)
+int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStream_t s);
+int prefix_graph(ps_graph *g, cudaStream_t s);
+int launch_sampler(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id,
+                   uint64_t *d_hist, cudaStream_t s);
+int launch_batch(const void *d_table, int32_t n_graphs, const ps_work *d_items, int64_t n_items,
+                 uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s);
+
+}  // namespace ps

@@ -1,0 +1,645 @@
+// ps_load.cu -- ps_load_csr: validation of the input graph (Section 2), the
+// degree order of Section 4 made the integer order by relabelling, sorted
+// adjacency lists, and the edge table (u < v, row-major) with the position of
+// each edge in both endpoint lists.
+#include <climits>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+// ------------------------------------------------------------ scan plumbing
+
+template <typename T>
+ScanState<T> scan_state(ps_graph *g, int counter_slot) {
+    ScanState<T> s;
+    s.flag = reinterpret_cast<uint32_t *>(g->ws + g->L.scan_flag);
+    s.agg = reinterpret_cast<T *>(g->ws + g->L.scan_agg);
+    s.inc = reinterpret_cast<T *>(g->ws + g->L.scan_inc);
+    s.counter = reinterpret_cast<uint32_t *>(g->status + ST_COUNTER + counter_slot);
+    s.status = g->status;
+    return s;
+}
+template ScanState<uint32_t> scan_state<uint32_t>(ps_graph *, int);
+template ScanState<int64_t> scan_state<int64_t>(ps_graph *, int);
+template ScanState<int32_t> scan_state<int32_t>(ps_graph *, int);
+template ScanState<U64x2> scan_state<U64x2>(ps_graph *, int);
+
+int reset_scan(ps_graph *g, int counter_slot, int64_t count, cudaStream_t s) {
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    if (tiles > g->L.scan_tiles) return PS_ERR_WORKSPACE;
+    PS_CUDA_TRY(cudaMemsetAsync(g->ws + g->L.scan_flag, 0, sizeof(uint32_t) * (tiles + 1), s));
+    PS_CUDA_TRY(cudaMemsetAsync(g->status + ST_COUNTER + counter_slot, 0, sizeof(uint64_t), s));
+    return PS_OK;
+}
+
+template <typename T, typename Op, typename Load, typename Store>
+static int run_scan(ps_graph *g, int slot, int64_t count, T identity, Op op, Load load, Store store,
+                    cudaStream_t s) {
+    if (count <= 0) return PS_OK;
+    int rc = reset_scan(g, slot, count, s);
+    if (rc) return rc;
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    k_scan<T, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
+        count, scan_state<T>(g, slot), identity, op, load, store);
+    PS_CUDA_TRY(cudaGetLastError());
+    return PS_OK;
+}
+
+// ------------------------------------------------------------------ degrees
+
+__global__ void k_degrees(int64_t n, int64_t nnz, const int64_t *__restrict__ off,
+                          uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, u64 *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0) {
+        if (ldg_i64(off) != 0 || ldg_i64(off + n) != nnz) raise_flag(status, F_ARG);
+    }
+    uint32_t dmax = 0;
+    bool bad = false, longrow = false;
+    for (int64_t v = t0; v < n; v += stride) {
+        const int64_t a = ldg_i64(off + v), b = ldg_i64(off + v + 1);
+        int64_t d = b - a;
+        if (d < 0 || a < 0 || b > nnz) {
+            bad = true;
+            d = 0;
+        }
+        if (d > n - 1) longrow = true;  // cannot be a simple row
+        keys[v] = static_cast<uint32_t>(d);
+        vals[v] = static_cast<uint32_t>(v);
+        dmax = max(dmax, static_cast<uint32_t>(d));
+    }
+    if (bad) raise_flag(status, F_ARG);
+    if (longrow) raise_flag(status, F_NOT_SIMPLE);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax)
+        atomicMax(reinterpret_cast<unsigned long long *>(status + ST_DMAX), (unsigned long long)dmax);
+}
+
+// ------------------------------------------------ rank: stable LSD radix sort
+
+// Per-tile digit histogram, stored digit-major: counts[digit * tiles + tile].
+__global__ void __launch_bounds__(kRadixBlock)
+k_radix_hist(int64_t n, const uint32_t *__restrict__ keys, int shift, uint32_t *counts, int64_t tiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int i = threadIdx.x; i < kRadixTile; i += kRadixBlock) {
+        const int64_t idx = base + i;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: items are ranked round by round in input order; within a
+// round, lanes with equal digits are ranked by __match_any_sync and warps by
+// their per-digit counts.
+__global__ void __launch_bounds__(kRadixBlock)
+k_radix_scatter(int64_t n, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int shift,
+                const uint32_t *__restrict__ offsets, int64_t tiles) {
+    constexpr int NW = kRadixBlock / 32;
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wcnt[NW][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    s_base[threadIdx.x] = offsets[(int64_t)threadIdx.x * tiles + blockIdx.x];
+    for (int w = 0; w < NW; w++) s_wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int round = 0; round < kRadixItems; round++) {
+        const int64_t idx = base + (int64_t)round * kRadixBlock + threadIdx.x;
+        const bool valid = idx < n;
+        const uint32_t key = valid ? kin[idx] : 0u;
+        const uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t wrank = __popc(peers & lanemask_lt());
+        if (valid && lane == __ffs(peers) - 1) s_wcnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_base[digit] + wrank;
+            for (int w = 0; w < warp; w++) pos += s_wcnt[w][digit];
+            kout[pos] = key;
+            vout[pos] = vin[idx];
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int w = 0; w < NW; w++) {
+            tot += s_wcnt[w][threadIdx.x];
+            s_wcnt[w][threadIdx.x] = 0;
+        }
+        s_base[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+struct LoadU32 {
+    const uint32_t *p;
+    __device__ uint32_t operator()(int64_t i) const { return p[i]; }
+};
+struct StoreExclU32 {
+    uint32_t *p;
+    __device__ void operator()(int64_t i, uint32_t exc, uint32_t) const { p[i] = exc; }
+};
+
+// rank[v] = position of v in (degree, id) order; dnew[r] = degree of row r
+__global__ void k_rank(int64_t n, const uint32_t *__restrict__ skeys, const uint32_t *__restrict__ svals,
+                       int32_t *rank, int32_t *dnew, uint32_t *inv) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint32_t v = svals[r];
+        rank[v] = static_cast<int32_t>(r);
+        dnew[r] = static_cast<int32_t>(skeys[r]);
+        if (inv) inv[r] = v;
+    }
+}
+
+struct LoadDeg {
+    const int32_t *d;
+    __device__ int64_t operator()(int64_t i) const { return d[i]; }
+};
+struct StoreOffsets {
+    int64_t *off;
+    int64_t n;
+    __device__ void operator()(int64_t i, int64_t exc, int64_t inc) const {
+        off[i] = exc;
+        if (i == n - 1) off[n] = inc;
+    }
+};
+
+// first row whose degree exceeds each tier limit (rows are degree-sorted)
+__global__ void k_tiers(int64_t n, const int32_t *__restrict__ dnew, u64 *status) {
+    const int lim[4] = {0, kTierA, kTierB, kTierC};
+    const int t = threadIdx.x;
+    if (t < 4) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (dnew[mid] > lim[t]) hi = mid;
+            else lo = mid + 1;
+        }
+        status[ST_TIER + t] = static_cast<u64>(lo);
+    }
+    if (t == 4) status[ST_TIER + 4] = static_cast<u64>(n);
+}
+
+// ------------------------------------------------------- row relabel + sort
+
+struct RowIn {
+    const int64_t *off;
+    const int32_t *col;
+    const uint32_t *inv;   // row r of the new graph is input vertex inv[r]
+    const int32_t *rank;
+    const int64_t *coff;
+    int32_t *ccol;
+    int32_t *lowcnt;
+    int64_t n;
+    u64 *status;
+};
+
+// Relabelled neighbour, with range and self-loop checks (the bad column is
+// replaced by the row itself so no access leaves the arrays).
+__device__ __forceinline__ int32_t relabel(const RowIn &R, int64_t i, uint32_t v, int32_t r,
+                                          bool &bad_arg, bool &self) {
+    const int32_t c = ldg_i32(R.col + i);
+    if (c < 0 || c >= R.n) {
+        bad_arg = true;
+        return r;
+    }
+    if (c == static_cast<int32_t>(v)) self = true;
+    return ldg_i32(R.rank + c);
+}
+
+__device__ __forceinline__ void report(const RowIn &R, bool bad_arg, bool not_simple) {
+    if (bad_arg) raise_flag(R.status, F_ARG);
+    if (not_simple) raise_flag(R.status, F_NOT_SIMPLE);
+}
+
+// Tier A: rows of 1..32 entries, one warp, bitonic network in registers.
+__global__ void __launch_bounds__(256) k_sort_tier_a(RowIn R) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 0]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 1]);
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    bool bad = false, nsimple = false;
+    for (int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < r1; r += nw) {
+        const uint32_t v = R.inv[r];
+        const int64_t o = ldg_i64(R.off + v);
+        const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
+        int32_t x = INT_MAX;
+        if (lane < d) x = relabel(R, o + lane, v, (int32_t)r, bad, nsimple);
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                const bool asc = (lane & k) == 0, lower = (lane & j) == 0;
+                x = (lower == asc) ? min(x, y) : max(x, y);
+            }
+        }
+        const int32_t nx = __shfl_down_sync(0xffffffffu, x, 1);
+        if (lane + 1 < d && nx == x) nsimple = true;
+        const uint32_t low = __popc(__ballot_sync(0xffffffffu, lane < d && x < (int32_t)r));
+        if (lane < d) R.ccol[R.coff[r] + lane] = x;
+        if (lane == 0) R.lowcnt[r] = (int32_t)low;
+    }
+    report(R, bad, nsimple);
+}
+
+__device__ __forceinline__ int next_pow2(int d) {
+    int p = 1;
+    while (p < d) p <<= 1;
+    return p;
+}
+
+// Tier B: rows of 33..1024 entries, one warp, bitonic network in shared memory.
+__global__ void __launch_bounds__(256) k_sort_tier_b(RowIn R) {
+    __shared__ int32_t s_buf[8][kTierB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *buf = s_buf[warp];
+    const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 1]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 2]);
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    bool bad = false, nsimple = false;
+    for (int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < r1; r += nw) {
+        const uint32_t v = R.inv[r];
+        const int64_t o = ldg_i64(R.off + v);
+        const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
+        const int P = next_pow2(d);
+        for (int i = lane; i < P; i += 32)
+            buf[i] = (i < d) ? relabel(R, o + i, v, (int32_t)r, bad, nsimple) : INT_MAX;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < (P >> 1); i += 32) {
+                    const int e = 2 * i - (i & (j - 1));
+                    const int32_t a = buf[e], b = buf[e + j];
+                    const bool asc = (e & k) == 0;
+                    if ((a > b) == asc) {
+                        buf[e] = b;
+                        buf[e + j] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int low = 0;
+        int32_t *dst = R.ccol + R.coff[r];
+        for (int i = lane; i < d; i += 32) {
+            const int32_t x = buf[i];
+            dst[i] = x;
+            low += (x < (int32_t)r);
+            if (i + 1 < d && buf[i + 1] == x) nsimple = true;
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+        if (lane == 0) R.lowcnt[r] = low;
+        __syncwarp();
+    }
+    report(R, bad, nsimple);
+}
+
+// Tier C: rows of 1025..32768 entries, one block of 1024, shared-memory bitonic.
+__global__ void __launch_bounds__(1024) k_sort_tier_c(RowIn R) {
+    extern __shared__ int32_t s_dyn[];
+    __shared__ int s_low;
+    const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 2]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 3]);
+    bool bad = false, nsimple = false;
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const uint32_t v = R.inv[r];
+        const int64_t o = ldg_i64(R.off + v);
+        const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
+        const int P = next_pow2(d);
+        if (threadIdx.x == 0) s_low = 0;
+        for (int i = threadIdx.x; i < P; i += blockDim.x)
+            s_dyn[i] = (i < d) ? relabel(R, o + i, v, (int32_t)r, bad, nsimple) : INT_MAX;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                    const int e = 2 * i - (i & (j - 1));
+                    const int32_t a = s_dyn[e], b = s_dyn[e + j];
+                    const bool asc = (e & k) == 0;
+                    if ((a > b) == asc) {
+                        s_dyn[e] = b;
+                        s_dyn[e + j] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        int low = 0;
+        int32_t *dst = R.ccol + R.coff[r];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const int32_t x = s_dyn[i];
+            dst[i] = x;
+            low += (x < (int32_t)r);
+            if (i + 1 < d && s_dyn[i + 1] == x) nsimple = true;
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_low, low);
+        __syncthreads();
+        if (threadIdx.x == 0) R.lowcnt[r] = s_low;
+        __syncthreads();
+    }
+    report(R, bad, nsimple);
+}
+
+// Tier D: rows above 32768 entries, one block of 1024, stable LSD radix sort
+// (8-bit digits) ping-ponging between the output row and a scratch row.
+__global__ void __launch_bounds__(1024) k_sort_tier_d(RowIn R, int32_t *tmp, int bits) {
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wcnt[32][256];
+    __shared__ int s_low;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 3]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 4]);
+    const int64_t tbase = (r0 < r1) ? R.coff[r0] : 0;
+    bool bad = false, nsimple = false;
+    for (int w = 0; w < 32; w++)
+        if (threadIdx.x < 256) s_wcnt[w][threadIdx.x] = 0;
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const uint32_t v = R.inv[r];
+        const int64_t o = ldg_i64(R.off + v);
+        const int64_t d = ldg_i64(R.off + v + 1) - o;
+        int32_t *out = R.ccol + R.coff[r];
+        int32_t *scr = tmp + (R.coff[r] - tbase);
+        for (int64_t i = threadIdx.x; i < d; i += blockDim.x)
+            scr[i] = relabel(R, o + i, v, (int32_t)r, bad, nsimple);
+        __syncthreads();
+        int32_t *src = scr, *dst = out;
+        for (int shift = 0; shift < bits; shift += 8) {
+            if (threadIdx.x < 256) s_hist[threadIdx.x] = 0;
+            __syncthreads();
+            for (int64_t i = threadIdx.x; i < d; i += blockDim.x)
+                atomicAdd(&s_hist[(static_cast<uint32_t>(src[i]) >> shift) & 255u], 1u);
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t h[8], run = 0;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    h[q] = s_hist[lane * 8 + q];
+                    run += h[q];
+                }
+                uint32_t x = run;
+#pragma unroll
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o2);
+                    if (lane >= o2) x += y;
+                }
+                uint32_t e = x - run;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    s_base[lane * 8 + q] = e;
+                    e += h[q];
+                }
+            }
+            __syncthreads();
+            for (int64_t i0 = 0; i0 < d; i0 += blockDim.x) {
+                const int64_t i = i0 + threadIdx.x;
+                const bool valid = i < d;
+                const int32_t x = valid ? src[i] : 0;
+                const uint32_t digit = valid ? ((static_cast<uint32_t>(x) >> shift) & 255u) : 256u;
+                const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+                const uint32_t wrank = __popc(peers & lanemask_lt());
+                if (valid && lane == __ffs(peers) - 1) s_wcnt[warp][digit] = __popc(peers);
+                __syncthreads();
+                if (valid) {
+                    uint32_t pos = s_base[digit] + wrank;
+                    for (int w = 0; w < warp; w++) pos += s_wcnt[w][digit];
+                    dst[pos] = x;
+                }
+                __syncthreads();
+                if (threadIdx.x < 256) {
+                    uint32_t tot = 0;
+                    for (int w = 0; w < 32; w++) {
+                        tot += s_wcnt[w][threadIdx.x];
+                        s_wcnt[w][threadIdx.x] = 0;
+                    }
+                    s_base[threadIdx.x] += tot;
+                }
+                __syncthreads();
+            }
+            int32_t *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != out) {
+            for (int64_t i = threadIdx.x; i < d; i += blockDim.x) out[i] = src[i];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_low = 0;
+        __syncthreads();
+        int low = 0;
+        for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+            const int32_t x = out[i];
+            low += (x < (int32_t)r);
+            if (i + 1 < d && out[i + 1] == x) nsimple = true;
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+        if (lane == 0) atomicAdd(&s_low, low);
+        __syncthreads();
+        if (threadIdx.x == 0) R.lowcnt[r] = s_low;
+        __syncthreads();
+    }
+    report(R, bad, nsimple);
+}
+
+// ------------------------------------------------------------- edge table
+
+struct LoadUp {
+    const int32_t *dnew;
+    const int32_t *low;
+    __device__ int64_t operator()(int64_t i) const { return (int64_t)dnew[i] - low[i]; }
+};
+struct StoreUbase {
+    int64_t *ubase;
+    int64_t n;
+    u64 *status;
+    __device__ void operator()(int64_t i, int64_t exc, int64_t inc) const {
+        ubase[i] = exc;
+        if (i == n - 1) {
+            ubase[n] = inc;
+            status[ST_M_UPPER] = static_cast<u64>(inc);
+        }
+    }
+};
+
+// Edge j = (u, v), u < v, in row-major order: j = ubase[u] + (iu - lowcnt[u]).
+// Upper arcs (u -> v) fill u, v, d_u, d_v, iu, off_u, off_v; lower arcs
+// (v -> u, at position jv of N(v)) find v in the upper part of N(u) and fill
+// jv.  A lower arc without its upper partner means an asymmetric input.
+constexpr int kEdgeItems = 8;
+__global__ void __launch_bounds__(256)
+k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+        const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, EdgeRec *rec,
+        int64_t m_cap, u64 *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool asym = false;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c * kEdgeItems < nnz; c += stride) {
+        const int64_t i0 = c * kEdgeItems;
+        int64_t lo = 0, hi = n;  // last row r with coff[r] <= i0
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (ldg_i64(coff + mid) <= i0) lo = mid;
+            else hi = mid - 1;
+        }
+        int64_t r = lo;
+        int64_t rend = ldg_i64(coff + r + 1);
+        for (int t = 0; t < kEdgeItems; t++) {
+            const int64_t i = i0 + t;
+            if (i >= nnz) break;
+            while (rend <= i) {
+                r++;
+                rend = ldg_i64(coff + r + 1);
+            }
+            const int64_t ro = ldg_i64(coff + r);
+            const int32_t p = static_cast<int32_t>(i - ro);
+            const int32_t x = ldg_i32(ccol + i);
+            if (x > r) {
+                const int64_t j = ldg_i64(ubase + r) + p - ldg_i32(lowcnt + r);
+                if (j < 0 || j >= m_cap) {
+                    asym = true;
+                    continue;
+                }
+                const int64_t ox = ldg_i64(coff + x);
+                const int64_t dx = ldg_i64(coff + x + 1) - ox;
+                int32_t *e = reinterpret_cast<int32_t *>(rec + j);
+                *reinterpret_cast<int4 *>(e) =
+                    make_int4((int32_t)r, x, (int32_t)(rend - ro), (int32_t)dx);
+                e[4] = p;
+                *reinterpret_cast<int2 *>(e + 6) = make_int2((int32_t)ro, (int32_t)ox);
+            } else if (x < r) {
+                const int64_t ox = ldg_i64(coff + x);
+                const int32_t lx = ldg_i32(lowcnt + x);
+                const int64_t dx = ldg_i64(coff + x + 1) - ox;
+                int64_t a = ox + lx, b = ox + dx;  // lower_bound of r in the upper part
+                while (a < b) {
+                    const int64_t mid = (a + b) >> 1;
+                    if (ldg_i32(ccol + mid) < r) a = mid + 1;
+                    else b = mid;
+                }
+                if (a >= ox + dx || ldg_i32(ccol + a) != (int32_t)r) {
+                    asym = true;
+                    continue;
+                }
+                const int64_t j = ldg_i64(ubase + x) + (a - ox - lx);
+                if (j < 0 || j >= m_cap) {
+                    asym = true;
+                    continue;
+                }
+                reinterpret_cast<int32_t *>(rec + j)[5] = p;
+            }
+        }
+    }
+    if (asym) raise_flag(status, F_ASYM);
+}
+
+// ------------------------------------------------------------------- driver
+
+int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStream_t s) {
+    const Layout &L = g->L;
+    const int64_t n = L.n, nnz = L.nnz;
+    char *ws = g->ws;
+    const int sms = g->sm_count;
+    PS_CUDA_TRY(cudaMemsetAsync(g->status, 0, ST_WORDS * sizeof(uint64_t), s));
+    PS_CUDA_TRY(cudaMemsetAsync(g->lowcnt, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    uint32_t *k0 = reinterpret_cast<uint32_t *>(ws + L.keys0);
+    uint32_t *k1 = reinterpret_cast<uint32_t *>(ws + L.keys1);
+    uint32_t *v0 = reinterpret_cast<uint32_t *>(ws + L.vals0);
+    uint32_t *v1 = reinterpret_cast<uint32_t *>(ws + L.vals1);
+
+    // (1) degrees and offset validation; nothing else may index with bad offsets
+    k_degrees<<<sms * 8, 256, 0, s>>>(n, nnz, d_off, k0, v0, g->status);
+    PS_CUDA_TRY(cudaGetLastError());
+    uint64_t st[ST_WORDS];
+    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[ST_FLAGS] & F_ARG) return PS_ERR_ARG;
+    g->d_max = static_cast<int64_t>(st[ST_DMAX]);
+
+    // (2) stable LSD radix sort of (degree, id): ties keep increasing id
+    int bits = 0;
+    while (bits < 32 && (static_cast<uint64_t>(g->d_max) >> bits) != 0) bits++;
+    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + L.rcounts);
+    const int64_t tiles = L.radix_tiles;
+    for (int shift = 0; shift < bits && n > 0; shift += 8) {
+        k_radix_hist<<<(unsigned)tiles, kRadixBlock, 0, s>>>(n, k0, shift, counts, tiles);
+        PS_CUDA_TRY(cudaGetLastError());
+        int rc = run_scan<uint32_t>(g, 0, 256 * tiles, 0u, OpSum(), LoadU32{counts},
+                                    StoreExclU32{counts}, s);
+        if (rc) return rc;
+        k_radix_scatter<<<(unsigned)tiles, kRadixBlock, 0, s>>>(n, k0, v0, k1, v1, shift, counts,
+                                                                tiles);
+        PS_CUDA_TRY(cudaGetLastError());
+        uint32_t *t = k0;
+        k0 = k1;
+        k1 = t;
+        t = v0;
+        v0 = v1;
+        v1 = t;
+    }
+    // k0/v0 hold the sorted (degree, vertex) pairs; v1 receives inv[r]
+    if (n > 0) {
+        k_rank<<<sms * 8, 256, 0, s>>>(n, k0, v0, g->rank, g->dnew, v1);
+        PS_CUDA_TRY(cudaGetLastError());
+    }
+    const uint32_t *inv = v1;
+    PS_CUDA_TRY(cudaMemsetAsync(g->off, 0, sizeof(int64_t), s));
+    int rc = run_scan<int64_t>(g, 1, n, (int64_t)0, OpSum(), LoadDeg{g->dnew}, StoreOffsets{g->off, n}, s);
+    if (rc) return rc;
+    k_tiers<<<1, 32, 0, s>>>(n, g->dnew, g->status);
+    PS_CUDA_TRY(cudaGetLastError());
+
+    // (3) relabel + sort every row, by tier
+    RowIn R{d_off, d_col, inv, g->rank, g->off, g->col, g->lowcnt, n, g->status};
+    if (n > 0) {
+        k_sort_tier_a<<<sms * 16, 256, 0, s>>>(R);
+        PS_CUDA_TRY(cudaGetLastError());
+        k_sort_tier_b<<<sms * 4, 256, 0, s>>>(R);
+        PS_CUDA_TRY(cudaGetLastError());
+        if (g->d_max > kTierB) {
+            const int smem = kTierC * (int)sizeof(int32_t);
+            PS_CUDA_TRY(cudaFuncSetAttribute(k_sort_tier_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_sort_tier_c<<<sms, 1024, smem, s>>>(R);
+            PS_CUDA_TRY(cudaGetLastError());
+        }
+        if (g->d_max > kTierC) {
+            int vb = 0;
+            while (vb < 31 && (static_cast<uint64_t>(n - 1) >> vb) != 0) vb++;
+            k_sort_tier_d<<<sms, 1024, 0, s>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
+            PS_CUDA_TRY(cudaGetLastError());
+        }
+    }
+
+    // (4) edge numbering and the edge table
+    PS_CUDA_TRY(cudaMemsetAsync(g->ubase, 0, sizeof(int64_t), s));
+    rc = run_scan<int64_t>(g, 2, n, (int64_t)0, OpSum(), LoadUp{g->dnew, g->lowcnt},
+                           StoreUbase{g->ubase, n, g->status}, s);
+    if (rc) return rc;
+    if (nnz > 0) {
+        int64_t chunks = (nnz + kEdgeItems - 1) / kEdgeItems;
+        int64_t blocks = (chunks + 255) / 256;
+        if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
+        k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->rec,
+                                                 L.m_cap, g->status);
+        PS_CUDA_TRY(cudaGetLastError());
+    }
+    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PS_CUDA_TRY(cudaStreamSynchronize(s));
+    const uint64_t m_upper = st[ST_M_UPPER];
+    uint64_t flags = st[ST_FLAGS];
+    if (2 * m_upper != static_cast<uint64_t>(nnz)) flags |= F_ASYM;
+    const int status = flags_to_status(flags);
+    if (status != PS_OK) return status;
+    g->m = static_cast<int64_t>(m_upper);
+    return PS_OK;
+}
+
+}  // namespace ps

@@ -1,0 +1,258 @@
+// ps_prefix.cu -- ps_tau_prefix: the edge weights of Section 3 (tau) and
+// Section 4 (lambda), their exact inclusive uint64 prefixes (the
+// distributions p_e of Alg. 1 / Alg. 3), N_1 of Alg. 2, the guide
+// tables that shorten the inverse-CDF search, and the hub bitmaps used by
+// the adjacency test.
+#include "ps_internal.h"
+
+namespace ps {
+
+// tau_j = (d_u - 1)(d_v - 1); lambda_j = L_{u,v} L_{v,u} with
+// L_{u,v} = d_u - 1 - iu (the neighbours of u after v in the order).
+__device__ __forceinline__ U64x2 weights(const EdgeRec &e) {
+    const uint64_t t = static_cast<uint64_t>(e.du - 1) * static_cast<uint64_t>(e.dv - 1);
+    const uint64_t l = static_cast<uint64_t>(e.du - 1 - e.iu) * static_cast<uint64_t>(e.dv - 1 - e.jv);
+    return U64x2{t, l};
+}
+
+struct LoadWeights {
+    const EdgeRec *rec;
+    __device__ U64x2 operator()(int64_t j) const { return weights(ldg_rec(rec + j)); }
+};
+struct StorePrefix {
+    uint64_t *ptau, *plam;
+    __device__ void operator()(int64_t j, U64x2, U64x2 inc) const {
+        ptau[j] = inc.a;
+        plam[j] = inc.b;
+    }
+};
+
+__device__ __forceinline__ void add128(uint64_t &lo, uint64_t &hi, uint64_t x) {
+    lo += x;
+    hi += (lo < x);
+}
+
+__device__ __forceinline__ void atomic_add128(u64 *pair, uint64_t lo, uint64_t hi) {
+    const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long *>(pair),
+                                             static_cast<unsigned long long>(lo));
+    if (old + lo < old) hi += 1;
+    if (hi) atomicAdd(reinterpret_cast<unsigned long long *>(pair + 1), static_cast<unsigned long long>(hi));
+}
+
+__device__ __forceinline__ void warp_add128(uint64_t &lo, uint64_t &hi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        add128(lo, hi, l2);
+        hi += h2;
+    }
+}
+
+// 128-bit sums of tau and lambda (W and Lambda must fit in 64 bits for the
+// prefixes to be exact).
+__global__ void __launch_bounds__(256) k_weight_totals(int64_t m, const EdgeRec *__restrict__ rec, u64 *status) {
+    uint64_t wl = 0, wh = 0, ll = 0, lh = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const U64x2 w = weights(ldg_rec(rec + j));
+        add128(wl, wh, w.a);
+        add128(ll, lh, w.b);
+    }
+    warp_add128(wl, wh);
+    warp_add128(ll, lh);
+    if ((threadIdx.x & 31) == 0) {
+        if (wl | wh) atomic_add128(status + ST_W_LO, wl, wh);
+        if (ll | lh) atomic_add128(status + ST_L_LO, ll, lh);
+    }
+}
+
+// N_1 = sum_v C(d_v, 3) (128-bit) and the number of hub rows: the top
+// `hub_cap` labels whose degree is at least kHubMinDegree.
+__global__ void __launch_bounds__(256)
+k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, u64 *status) {
+    uint64_t lo = 0, hi = 0;
+    unsigned long long hubs = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint64_t d = static_cast<uint64_t>(dnew[r]);
+        if (d >= 3) {
+            // d (d - 1) (d - 2) / 6 with d < 2^31: the product fits in 128 bits
+            const uint64_t a = d * (d - 1);  // < 2^62
+            const uint64_t b = d - 2;
+            uint64_t plo = a * b, phi = __umul64hi(a, b);
+            // divide the 128-bit product by 6 (exact)
+            const uint64_t qhi = phi / 6, rhi = phi % 6;
+            // (rhi * 2^64 + plo) / 6 with rhi < 6
+            const unsigned __int128 rest = (static_cast<unsigned __int128>(rhi) << 64) | plo;
+            const uint64_t qlo = static_cast<uint64_t>(rest / 6);
+            add128(lo, hi, qlo);
+            hi += qhi;
+        }
+        if (r >= n - hub_cap && d >= static_cast<uint64_t>(kHubMinDegree)) hubs++;
+    }
+    warp_add128(lo, hi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hubs += __shfl_down_sync(0xffffffffu, hubs, o);
+    if ((threadIdx.x & 31) == 0) {
+        if (lo | hi) atomic_add128(status + ST_N1_LO, lo, hi);
+        if (hubs) atomicAdd(reinterpret_cast<unsigned long long *>(status + ST_HUBS), hubs);
+    }
+}
+
+// Guide table: bucket b holds r in [b << shift, (b + 1) << shift).  Edge j
+// covers r in [P[j-1], P[j] - 1]; it marks the first bucket that starts in
+// its range, and an inclusive max-scan carries the mark over the following
+// buckets, so G[b] = the edge that the first r of bucket b selects.
+__global__ void k_guide_marks(int64_t m, const uint64_t *__restrict__ P, int shift, int32_t *G) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint64_t prev = j ? P[j - 1] : 0ull;
+        const uint64_t cur = P[j];
+        if (cur == prev) continue;
+        const uint64_t bstart = prev ? ((prev - 1) >> shift) + 1 : 0ull;
+        const uint64_t bend = (cur - 1) >> shift;
+        if (bstart <= bend) G[bstart] = static_cast<int32_t>(j);
+    }
+}
+
+struct LoadI32 {
+    const int32_t *p;
+    __device__ int32_t operator()(int64_t i) const { return p[i]; }
+};
+struct StoreGuide {
+    int32_t *G;
+    int64_t B;
+    int32_t last;
+    __device__ void operator()(int64_t i, int32_t, int32_t inc) const {
+        G[i] = inc;
+        if (i == B - 1) G[B] = last;
+    }
+};
+
+// One warp per hub row: set bit x of row h for every neighbour x.
+__global__ void __launch_bounds__(256)
+k_hub_bits(int64_t hub_start, int64_t n, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+           uint32_t *bits, int64_t words) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t r = hub_start + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < n; r += nw) {
+        uint32_t *row = bits + (r - hub_start) * words;
+        const int64_t o = coff[r], e = coff[r + 1];
+        for (int64_t i = o + lane; i < e; i += 32) {
+            const int32_t x = ccol[i];
+            atomicOr(row + (x >> 5), 1u << (x & 31));
+        }
+    }
+}
+
+static int guide_shift(uint64_t W, int64_t gcap) {
+    int s = 0;
+    while (s < 63 && (((W - 1) >> s) + 1) > static_cast<uint64_t>(gcap)) s++;
+    return s;
+}
+
+static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *G, int slot,
+                       int *shift_out, cudaStream_t s) {
+    const int64_t m = g->m;
+    const int shift = guide_shift(total, g->L.gcap);
+    const int64_t B = static_cast<int64_t>(((total - 1) >> shift) + 1);
+    *shift_out = shift;
+    PS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(int32_t) * (B + 1), s));
+    int64_t blocks = (m + 255) / 256;
+    if (blocks > (int64_t)g->sm_count * 32) blocks = (int64_t)g->sm_count * 32;
+    k_guide_marks<<<(unsigned)blocks, 256, 0, s>>>(m, P, shift, G);
+    PS_CUDA_TRY(cudaGetLastError());
+    int rc = reset_scan(g, slot, B, s);
+    if (rc) return rc;
+    const int64_t tiles = (B + kScanTile - 1) / kScanTile;
+    k_scan<int32_t, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
+        B, scan_state<int32_t>(g, slot), (int32_t)0, OpMax(), LoadI32{G},
+        StoreGuide{G, B, static_cast<int32_t>(m - 1)});
+    PS_CUDA_TRY(cudaGetLastError());
+    return PS_OK;
+}
+
+int prefix_graph(ps_graph *g, cudaStream_t s) {
+    const int64_t n = g->n, m = g->m;
+    const int sms = g->sm_count;
+    PS_CUDA_TRY(cudaMemsetAsync(g->status + ST_W_LO, 0, 7 * sizeof(uint64_t), s));
+    if (m > 0) {
+        int rc = reset_scan(g, 3, m, s);
+        if (rc) return rc;
+        const int64_t tiles = (m + kScanTile - 1) / kScanTile;
+        k_scan<U64x2, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
+            m, scan_state<U64x2>(g, 3), U64x2{0, 0}, OpSum(), LoadWeights{g->rec},
+            StorePrefix{g->ptau, g->plam});
+        PS_CUDA_TRY(cudaGetLastError());
+        k_weight_totals<<<sms * 8, 256, 0, s>>>(m, g->rec, g->status);
+        PS_CUDA_TRY(cudaGetLastError());
+    }
+    if (n > 0) {
+        k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->status);
+        PS_CUDA_TRY(cudaGetLastError());
+    }
+    uint64_t st[ST_WORDS];
+    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[ST_FLAGS] & F_TIMEOUT) return PS_ERR_TIMEOUT;
+    ps_stats &S = g->stats;
+    S.W = st[ST_W_LO];
+    S.Lambda = st[ST_L_LO];
+    S.N1_lo = st[ST_N1_LO];
+    S.N1_hi = st[ST_N1_HI];
+    S.n = n;
+    S.m = m;
+    S.d_max = g->d_max;
+    const bool overflow = st[ST_W_HI] != 0 || st[ST_L_HI] != 0;
+    if (overflow) return PS_ERR_OVERFLOW;
+
+    // guide tables (with guides off the table has at most 2 buckets)
+    int tshift = 0, lshift = 0;
+    if (S.W > 0) {
+        int rc = build_guide(g, g->ptau, S.W, g->gtau, 4, &tshift, s);
+        if (rc) return rc;
+    }
+    if (S.Lambda > 0) {
+        int rc = build_guide(g, g->plam, S.Lambda, g->glam, 5, &lshift, s);
+        if (rc) return rc;
+    }
+    S.tau_shift = tshift;
+    S.lambda_shift = lshift;
+
+    // hub bitmaps
+    const int64_t hubs = static_cast<int64_t>(st[ST_HUBS]);
+    S.hubs = hubs;
+    if (hubs > 0) {
+        PS_CUDA_TRY(cudaMemsetAsync(g->hub, 0, sizeof(uint32_t) * hubs * g->L.hub_words, s));
+        int64_t blocks = (hubs * 32 + 255) / 256;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        k_hub_bits<<<(unsigned)blocks, 256, 0, s>>>(n - hubs, n, g->off, g->col, g->hub, g->L.hub_words);
+        PS_CUDA_TRY(cudaGetLastError());
+    }
+    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[ST_FLAGS] & F_TIMEOUT) return PS_ERR_TIMEOUT;
+
+    GraphDev &D = g->dev;
+    D.off = g->off;
+    D.col = g->col;
+    D.rec = g->rec;
+    D.ptau = g->ptau;
+    D.plam = g->plam;
+    D.gtau = g->gtau;
+    D.glam = g->glam;
+    D.hub = g->hub;
+    D.W = S.W;
+    D.Lambda = S.Lambda;
+    D.n = n;
+    D.m = m;
+    D.hub_start = static_cast<int32_t>(n - hubs);
+    D.hub_words = static_cast<int32_t>(g->L.hub_words);
+    D.tau_shift = tshift;
+    D.lam_shift = lshift;
+    g->prefixed = true;
+    return (S.W == 0 || S.Lambda == 0) ? PS_NO_PATHS : PS_OK;
+}
+
+}  // namespace ps

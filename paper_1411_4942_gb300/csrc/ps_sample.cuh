@@ -1,0 +1,98 @@
+// ps_sample.cuh -- one draw of Alg. 1 (sample) and of Alg. 3
+// (sample-centered), classified as in Alg. 2 / Alg. 4.
+//
+// Draw rules (identical to the CPU replay): sample `id` reads Philox block 0
+// of counter (id, 0, sampler); the edge draw r uniform in [0, W) takes words
+// 0-1, the neighbour draws words 2 and 3 (Lemire, rejected attempts walk
+// blocks 1, 2, ...).  The edge is the first j with P[j] > r.
+#pragma once
+
+#include "ps_device.cuh"
+
+namespace ps {
+
+// Class of one Alg. 1 output: 0 = triangle (u' == v'), 1 = 3-path,
+// 2 = tailed triangle, 3 = 4-cycle, 4 = chordal 4-cycle, 5 = 4-clique.
+__device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, uint64_t id) {
+    const uint4 w = sample_block(seed, id, 0, 0);
+    uint64_t r;
+    if (!lemire64((static_cast<uint64_t>(w.y) << 32) | w.x, g.W, r)) r = draw_r_retry(seed, id, 0, g.W);
+    const int64_t j = find_edge(g.ptau, g.gtau, g.tau_shift, r);
+    const EdgeRec e = ldg_rec(g.rec + j);
+    // u' uniform over N(u) \ {v}: a in [0, d_u - 1), the slot of v maps to the last entry
+    const uint32_t su = static_cast<uint32_t>(e.du - 1), sv = static_cast<uint32_t>(e.dv - 1);
+    uint32_t a, b;
+    if (!lemire32(w.z, su, a)) a = draw_small_retry(seed, id, 0, 2, su);
+    if (!lemire32(w.w, sv, b)) b = draw_small_retry(seed, id, 0, 3, sv);
+    const int32_t pa = (a == static_cast<uint32_t>(e.iu)) ? e.du - 1 : static_cast<int32_t>(a);
+    const int32_t pb = (b == static_cast<uint32_t>(e.jv)) ? e.dv - 1 : static_cast<int32_t>(b);
+    const int32_t up = ldg_i32(g.col + e.ou + pa);
+    const int32_t vp = ldg_i32(g.col + e.ov + pb);
+    if (up == vp) return 0;
+    // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
+    const bool e1 = (up < e.v) ? adjacent(g, up, e.v) : adjacent_known(g, e.v, e.ov, e.dv, up);
+    const bool e2 = (e.u < vp) ? adjacent_known(g, e.u, e.ou, e.du, vp) : adjacent(g, vp, e.u);
+    const bool e3 = adjacent(g, up, vp);
+    const int s = (int)e1 + (int)e2 + (int)e3;
+    return s == 0 ? 1 : (s == 1 ? (e3 ? 3 : 2) : (s == 2 ? 4 : 5));
+}
+
+// Class of one Alg. 3 output: 0 = not centred, 1 = 4-cycle, 2 = chordal
+// 4-cycle, 3 = 4-clique.  u' is drawn among the L_{u,v} entries of N(u)
+// after v, v' among the L_{v,u} entries of N(v) after u; the path is centred
+// (Definition 4.1) iff (u', v') is an edge.
+__device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, uint64_t id) {
+    const uint4 w = sample_block(seed, id, 0, 1);
+    uint64_t r;
+    if (!lemire64((static_cast<uint64_t>(w.y) << 32) | w.x, g.Lambda, r))
+        r = draw_r_retry(seed, id, 1, g.Lambda);
+    const int64_t j = find_edge(g.plam, g.glam, g.lam_shift, r);
+    const EdgeRec e = ldg_rec(g.rec + j);
+    const uint32_t lu = static_cast<uint32_t>(e.du - 1 - e.iu);
+    const uint32_t lv = static_cast<uint32_t>(e.dv - 1 - e.jv);
+    uint32_t a, b;
+    if (!lemire32(w.z, lu, a)) a = draw_small_retry(seed, id, 1, 2, lu);
+    if (!lemire32(w.w, lv, b)) b = draw_small_retry(seed, id, 1, 3, lv);
+    const int32_t up = ldg_i32(g.col + e.ou + e.iu + 1 + static_cast<int32_t>(a));
+    const int32_t vp = ldg_i32(g.col + e.ov + e.jv + 1 + static_cast<int32_t>(b));
+    if (!adjacent(g, up, vp)) return 0;  // also covers u' == v'
+    // u' > v and v' > u in label order, so the chord tests search N(v) and N(u)
+    const bool c1 = adjacent_known(g, e.v, e.ov, e.dv, up);
+    const bool c2 = adjacent_known(g, e.u, e.ou, e.du, vp);
+    return 1 + (int)c1 + (int)c2;
+}
+
+// Per-thread class counters kept in registers.
+struct Counts6 {
+    uint32_t c[6];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 6; i++) c[i] = 0;
+    }
+    __device__ __forceinline__ void add(int cls) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) c[i] += (cls == i);
+    }
+};
+
+// Block-wide sum of the counters, added to hist[0..nbins) with one atomic per
+// bin per block.
+template <int BLOCK>
+__device__ __forceinline__ void flush_counts(Counts6 &cnt, int nbins, uint64_t *hist) {
+    __shared__ unsigned long long s_bins[6];
+    if (threadIdx.x < 6) s_bins[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        unsigned long long x = cnt.c[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_bins[i], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < nbins && s_bins[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(hist + threadIdx.x), s_bins[threadIdx.x]);
+    __syncthreads();
+}
+
+}  // namespace ps

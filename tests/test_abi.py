@@ -1,0 +1,52 @@
+"""The C interface: the library builds for sm_103a, loads, and exports every
+function include/pathsample.h declares.  No GPU needed (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1411_4942_gb300 import _build
+from paper_1411_4942_gb300 import pathsample as ps
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ps_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = _build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(ps.EXPORTED) <= declared
+
+
+def test_built_for_sm_103a_only():
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings_and_workspace_sizes():
+    assert ps.ps_strerror(0) == "ok"
+    assert "symmetric" in ps.ps_strerror(ps.PS_ERR_ASYMMETRIC)
+    a = ps.ps_graph_workspace_bytes(1000, 10000)
+    b = ps.ps_graph_workspace_bytes(1000, 20000)
+    assert 0 < a < b and a % 256 == 0
+    assert ps.ps_graph_workspace_bytes(0, 0) > 0
+    assert ps.ps_graph_workspace_bytes(-1, 0) == 0
+    assert ps.ps_graph_workspace_bytes(1 << 31, 10) == 0  # labels must fit in int32
+    # hubs and guide tables change the size, never the results
+    t_off = ps.make_tuning(hub_count=-1, guide_log2_ratio=-1)
+    assert ps.ps_graph_workspace_bytes(100000, 1000000, t_off) < ps.ps_graph_workspace_bytes(100000, 1000000)
+    assert ps.ps_end_to_end_workspace_bytes(1000, 10000) > a
