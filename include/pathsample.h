@@ -141,6 +141,10 @@ void ps_graph_free(ps_graph *g);
 /* Short description of a status code (static string). */
 const char *ps_strerror(int code);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all devices and threads).  For launch accounting in benchmarks. */
+uint64_t ps_kernel_launches(void);
+
 /* Which array ps_graph_copy copies out. */
 #define PS_ARRAY_OFFSETS 0 /* int64 [n + 1]   canonical row offsets                      */
 #define PS_ARRAY_COLUMNS 1 /* int32 [nnz]     canonical sorted adjacency                 */

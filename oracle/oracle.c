@@ -67,12 +67,6 @@ typedef unsigned __int128 u128;
  * priority: offsets well formed and columns in range (OR_ERR_ARG); no
  * self-loop and no repeated neighbour (OR_ERR_NOT_SIMPLE); every arc has its
  * reverse (OR_ERR_ASYMMETRIC).  Rows need not be sorted. */
-static int has_arc(const int64_t *off, const int32_t *col, int32_t x, int32_t y) {
-    for (int64_t i = off[x]; i < off[x + 1]; i++)
-        if (col[i] == y) return 1;
-    return 0;
-}
-
 static int cmp_i32(const void *a, const void *b) {
     int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
     return (x > y) - (x < y);
@@ -85,24 +79,33 @@ int or_validate(int64_t n, int64_t nnz, const int64_t *off, const int32_t *col) 
         if (off[v + 1] < off[v]) return OR_ERR_ARG;
     for (int64_t i = 0; i < nnz; i++)
         if (col[i] < 0 || col[i] >= n) return OR_ERR_ARG;
+    /* sorted copy of every row: repeated neighbours become adjacent, and the
+     * reverse-arc lookups below can bisect */
+    int32_t *scol = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!scol) return OR_ERR_NOMEM;
+    memcpy(scol, col, (size_t)nnz * sizeof(int32_t));
     int bad_simple = 0;
-    for (int64_t v = 0; v < n && !bad_simple; v++) {
+    for (int64_t v = 0; v < n; v++) {
+        int32_t *row = scol + off[v];
         int64_t d = off[v + 1] - off[v];
-        int32_t *row = (int32_t *)malloc((size_t)(d > 0 ? d : 1) * sizeof(int32_t));
-        if (!row) return OR_ERR_NOMEM;
-        memcpy(row, col + off[v], (size_t)d * sizeof(int32_t));
         qsort(row, (size_t)d, sizeof(int32_t), cmp_i32);
         for (int64_t i = 0; i < d; i++) {
             if (row[i] == v) bad_simple = 1;
             if (i > 0 && row[i] == row[i - 1]) bad_simple = 1;
         }
-        free(row);
     }
-    if (bad_simple) return OR_ERR_NOT_SIMPLE;
-    for (int64_t v = 0; v < n; v++)
-        for (int64_t i = off[v]; i < off[v + 1]; i++)
-            if (!has_arc(off, col, col[i], (int32_t)v)) return OR_ERR_ASYMMETRIC;
-    return OR_OK;
+    int status = OR_OK;
+    if (bad_simple) status = OR_ERR_NOT_SIMPLE;
+    for (int64_t v = 0; v < n && status == OR_OK; v++)
+        for (int64_t i = off[v]; i < off[v + 1]; i++) {
+            int32_t w = col[i], key = (int32_t)v;
+            if (!bsearch(&key, scol + off[w], (size_t)(off[w + 1] - off[w]), sizeof(int32_t), cmp_i32)) {
+                status = OR_ERR_ASYMMETRIC;
+                break;
+            }
+        }
+    free(scol);
+    return status;
 }
 
 /* Section 4: u precedes v iff d_u < d_v, or d_u == d_v and id_u < id_v.

@@ -1,6 +1,7 @@
 // ps_api.cu -- the C entry points declared in include/pathsample.h: argument
 // checks, workspace layout, the FP64 estimates and error bars, the
 // end-to-end call and the batched-launch wrappers.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -33,7 +34,11 @@ struct DeviceGuard {
     }
 };
 
+std::atomic<unsigned long long> g_launches{0};
+
 }  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int sm_count_of_current_device() {
     int dev = 0, sms = 0;
@@ -303,6 +308,8 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const 
 }
 
 void ps_graph_free(ps_graph *g) { delete g; }
+
+uint64_t ps_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char *ps_strerror(int code) {
     switch (code) {

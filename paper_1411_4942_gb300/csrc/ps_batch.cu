@@ -56,7 +56,7 @@ static int launch_batch_t(const void *d_table, int32_t n_graphs, const ps_work *
     PS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s));
     k_batch<BLOCK><<<(unsigned)blocks, BLOCK, 0, s>>>(static_cast<const GraphDev *>(d_table), n_graphs,
                                                       d_items, n_items, d_hist, d_counter);
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
     return PS_OK;
 }
 

@@ -80,6 +80,15 @@ namespace ps {
 int sm_count_of_current_device();
 int flags_to_status(uint64_t flags);
 
+// Every kernel launch is followed by this: counts the launch (reported by
+// ps_kernel_launches) and checks the launch error.
+void count_launch();
+#define PS_LAUNCH_CHECK()                       \
+    do {                                        \
+        ::ps::count_launch();                   \
+        PS_CUDA_TRY(cudaGetLastError());        \
+    } while (0)
+
 // scan helpers (ps_load.cu)
 template <typename T>
 ScanState<T> scan_state(ps_graph *g, int counter_slot);

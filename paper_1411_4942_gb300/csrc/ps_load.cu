@@ -42,7 +42,7 @@ static int run_scan(ps_graph *g, int slot, int64_t count, T identity, Op op, Loa
     const int64_t tiles = (count + kScanTile - 1) / kScanTile;
     k_scan<T, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
         count, scan_state<T>(g, slot), identity, op, load, store);
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
     return PS_OK;
 }
 
@@ -557,7 +557,7 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
 
     // (1) degrees and offset validation; nothing else may index with bad offsets
     k_degrees<<<sms * 8, 256, 0, s>>>(n, nnz, d_off, k0, v0, g->status);
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
     uint64_t st[ST_WORDS];
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -571,13 +571,13 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     const int64_t tiles = L.radix_tiles;
     for (int shift = 0; shift < bits && n > 0; shift += 8) {
         k_radix_hist<<<(unsigned)tiles, kRadixBlock, 0, s>>>(n, k0, shift, counts, tiles);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         int rc = run_scan<uint32_t>(g, 0, 256 * tiles, 0u, OpSum(), LoadU32{counts},
                                     StoreExclU32{counts}, s);
         if (rc) return rc;
         k_radix_scatter<<<(unsigned)tiles, kRadixBlock, 0, s>>>(n, k0, v0, k1, v1, shift, counts,
                                                                 tiles);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         uint32_t *t = k0;
         k0 = k1;
         k1 = t;
@@ -588,33 +588,33 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     // k0/v0 hold the sorted (degree, vertex) pairs; v1 receives inv[r]
     if (n > 0) {
         k_rank<<<sms * 8, 256, 0, s>>>(n, k0, v0, g->rank, g->dnew, v1);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
     }
     const uint32_t *inv = v1;
     PS_CUDA_TRY(cudaMemsetAsync(g->off, 0, sizeof(int64_t), s));
     int rc = run_scan<int64_t>(g, 1, n, (int64_t)0, OpSum(), LoadDeg{g->dnew}, StoreOffsets{g->off, n}, s);
     if (rc) return rc;
     k_tiers<<<1, 32, 0, s>>>(n, g->dnew, g->status);
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
 
     // (3) relabel + sort every row, by tier
     RowIn R{d_off, d_col, inv, g->rank, g->off, g->col, g->lowcnt, n, g->status};
     if (n > 0) {
         k_sort_tier_a<<<sms * 16, 256, 0, s>>>(R);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         k_sort_tier_b<<<sms * 4, 256, 0, s>>>(R);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         if (g->d_max > kTierB) {
             const int smem = kTierC * (int)sizeof(int32_t);
             PS_CUDA_TRY(cudaFuncSetAttribute(k_sort_tier_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             k_sort_tier_c<<<sms, 1024, smem, s>>>(R);
-            PS_CUDA_TRY(cudaGetLastError());
+            PS_LAUNCH_CHECK();
         }
         if (g->d_max > kTierC) {
             int vb = 0;
             while (vb < 31 && (static_cast<uint64_t>(n - 1) >> vb) != 0) vb++;
             k_sort_tier_d<<<sms, 1024, 0, s>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
-            PS_CUDA_TRY(cudaGetLastError());
+            PS_LAUNCH_CHECK();
         }
     }
 
@@ -629,7 +629,7 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
         k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->rec,
                                                  L.m_cap, g->status);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
     }
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -162,14 +162,14 @@ static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *
     int64_t blocks = (m + 255) / 256;
     if (blocks > (int64_t)g->sm_count * 32) blocks = (int64_t)g->sm_count * 32;
     k_guide_marks<<<(unsigned)blocks, 256, 0, s>>>(m, P, shift, G);
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
     int rc = reset_scan(g, slot, B, s);
     if (rc) return rc;
     const int64_t tiles = (B + kScanTile - 1) / kScanTile;
     k_scan<int32_t, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
         B, scan_state<int32_t>(g, slot), (int32_t)0, OpMax(), LoadI32{G},
         StoreGuide{G, B, static_cast<int32_t>(m - 1)});
-    PS_CUDA_TRY(cudaGetLastError());
+    PS_LAUNCH_CHECK();
     return PS_OK;
 }
 
@@ -184,13 +184,13 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         k_scan<U64x2, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
             m, scan_state<U64x2>(g, 3), U64x2{0, 0}, OpSum(), LoadWeights{g->rec},
             StorePrefix{g->ptau, g->plam});
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         k_weight_totals<<<sms * 8, 256, 0, s>>>(m, g->rec, g->status);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
     }
     if (n > 0) {
         k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->status);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
     }
     uint64_t st[ST_WORDS];
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -228,7 +228,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         int64_t blocks = (hubs * 32 + 255) / 256;
         if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
         k_hub_bits<<<(unsigned)blocks, 256, 0, s>>>(n - hubs, n, g->off, g->col, g->hub, g->L.hub_words);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
     }
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -36,7 +36,7 @@ static int launch_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first
         uint64_t blocks = (kk + BLOCK - 1) / BLOCK;
         if (blocks > full) blocks = full;
         k_sample<SAMPLER, BLOCK><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id, hist);
-        PS_CUDA_TRY(cudaGetLastError());
+        PS_LAUNCH_CHECK();
         k -= kk;
         first_id += kk;
     }

@@ -28,7 +28,7 @@ EXPORTED = [
     "ps_graph_workspace_bytes", "ps_load_csr", "ps_tau_prefix", "ps_sample_3paths",
     "ps_sample_centered", "ps_estimate", "ps_graph_free", "ps_strerror", "ps_graph_copy",
     "ps_end_to_end_workspace_bytes", "ps_count_motifs_host", "ps_batch_table_bytes",
-    "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared",
+    "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared", "ps_kernel_launches",
 ]
 
 
@@ -109,6 +109,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_batch_sample": ([V, I32, V, I64, V, V, V, V, V], I32),
             "ps_batch_prepare": ([V, I32, V, V], I32),
             "ps_batch_sample_prepared": ([V, I32, V, I64, V, V, V, V], I32),
+            "ps_kernel_launches": ([], U64),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -206,6 +207,10 @@ def ps_count_motifs_host(off: np.ndarray, col: np.ndarray, k3: int, kc: int, see
         d_workspace, ws_bytes, _tuning_ptr(tuning), _stream_ptr(stream), h6.ctypes.data,
         h4.ctypes.data, ctypes.byref(st), est.ctypes.data, lo.ctypes.data, hi.ctypes.data)
     return int(rc), est, lo, hi, h6, h4, st
+
+
+def ps_kernel_launches() -> int:
+    return int(load_library().ps_kernel_launches())
 
 
 def ps_batch_table_bytes(n_graphs: int) -> int:
