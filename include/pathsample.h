@@ -46,6 +46,7 @@ typedef struct CUstream_st *ps_stream_t; /* same type as cudaStream_t */
 #define PS_ERR_CUDA (-7)       /* a CUDA runtime call failed                     */
 #define PS_ERR_STATE (-8)      /* call out of order (e.g. sampling before prefix) */
 #define PS_ERR_NOMEM (-9)      /* host allocation failed                         */
+#define PS_ERR_TOO_LARGE (-10) /* input exceeds a fixed-size scratch limit        */
 
 /* Tuning knobs.  None of them changes any result; they only change speed.
  * Pass NULL for the defaults; a zero field also means "default". */
@@ -211,6 +212,34 @@ int ps_batch_prepare(const ps_graph *const *graphs, int32_t n_graphs, void *d_ta
 int ps_batch_sample_prepared(const void *d_table, int32_t n_graphs, const ps_work *d_items,
                              int64_t n_items, uint64_t *d_hist, uint32_t *d_counter,
                              const ps_tuning *t, ps_stream_t stream);
+
+/* ------------------------------------------------------ allocation-free */
+
+/* The paper has no counterpart to this call.  It is the exact prefix scan
+ * that ps_tau_prefix runs over the tau / lambda weights, offered to callers
+ * that cannot allocate device memory at all -- for example a plugin whose
+ * host application owns every byte of device memory through its own pool,
+ * or a serving process that reserved its whole HBM budget up front and must
+ * not add allocations (or their implicit synchronisation) while requests are
+ * in flight.  Such a caller can pass its own input and output buffers but no
+ * workspace.
+ *
+ * Computes d_pa[i] = d_a[0] + ... + d_a[i] and d_pb[i] = d_b[0] + ... + d_b[i]
+ * exactly in uint64 for i < count (device arrays; outputs may not alias the
+ * inputs).  The scan's scratch is a fixed array of about 2.3 MB inside the
+ * library that every GPU using the library keeps until the process exits;
+ * no device memory is allocated or freed and no allocating library routine
+ * is called.  The first call on each device looks up that array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (different streams or threads at once) race and give
+ * wrong results; issue them one after another.  Synchronises `stream`.
+ * Returns PS_ERR_TOO_LARGE (touching nothing) when count exceeds
+ * PS_PREFIX_STATIC_MAX_ITEMS, PS_ERR_OVERFLOW when a sum does not fit in
+ * 64 bits, PS_ERR_ARG for a negative count or a missing pointer. */
+#define PS_PREFIX_STATIC_MAX_ITEMS (1ll << 27)
+int ps_prefix_pairs_static(const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_pa,
+                           uint64_t *d_pb, int64_t count, ps_stream_t stream);
 
 #ifdef __cplusplus
 }

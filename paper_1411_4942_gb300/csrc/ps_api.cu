@@ -324,6 +324,7 @@ const char *ps_strerror(int code) {
         case PS_ERR_CUDA: return "CUDA runtime error";
         case PS_ERR_STATE: return "call out of order";
         case PS_ERR_NOMEM: return "host allocation failed";
+        case PS_ERR_TOO_LARGE: return "input larger than the fixed scratch of an allocation-free call";
         default: return "unknown status";
     }
 }

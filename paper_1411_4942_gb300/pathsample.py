@@ -110,6 +110,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_batch_prepare": ([V, I32, V, V], I32),
             "ps_batch_sample_prepared": ([V, I32, V, I64, V, V, V, V], I32),
             "ps_kernel_launches": ([], U64),
+            "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -211,6 +212,18 @@ def ps_count_motifs_host(off: np.ndarray, col: np.ndarray, k3: int, kc: int, see
 
 def ps_kernel_launches() -> int:
     return int(load_library().ps_kernel_launches())
+
+
+PS_ERR_TOO_LARGE = -10
+PS_PREFIX_STATIC_MAX_ITEMS = 1 << 27
+
+
+def ps_prefix_pairs_static(d_a, d_b, d_pa, d_pb, count: int, stream=None) -> int:
+    """Exact uint64 prefix sums of two device arrays with no device allocation
+    (scratch is a fixed array inside the library); for callers that cannot
+    allocate device memory."""
+    return int(load_library().ps_prefix_pairs_static(d_a, d_b, d_pa, d_pb, count,
+                                                     _stream_ptr(stream)))
 
 
 def ps_batch_table_bytes(n_graphs: int) -> int:
