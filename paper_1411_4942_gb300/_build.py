@@ -37,15 +37,17 @@ def _tag(extra=()) -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every translation unit in parallel and link the shared library."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_path: str | None = None) -> str:
+    """Compile every translation unit in parallel and link the shared library
+    (to out_path when given, e.g. a variant built with extra -D flags)."""
+    lib_path = out_path or LIB_PATH
     tag = _tag(extra_flags)
-    tag_path = LIB_PATH + ".tag"
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(tag_path):
+    tag_path = lib_path + ".tag"
+    if not force and os.path.exists(lib_path) and os.path.exists(tag_path):
         with open(tag_path) as f:
             if f.read().strip() == tag:
-                return LIB_PATH
-    obj_dir = os.path.join(PKG, "_build")
+                return lib_path
+    obj_dir = os.path.join(PKG, "_build", tag)
     os.makedirs(obj_dir, exist_ok=True)
 
     def compile_one(src):
@@ -62,15 +64,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(tag_path, "w") as f:
         f.write(tag)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":

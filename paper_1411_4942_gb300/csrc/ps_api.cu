@@ -62,11 +62,13 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
     r.blocks_per_sm = 0;
     r.guide_log2_ratio = 1;
     r.samples_per_thread = 1;
-    // default hub rows: up to 1024 bitmap rows within 256 MB
+    r.adj_mode = kAdjHash;
+    if (t && (t->adjacency == kAdjSearch || t->adjacency == kAdjVtab)) r.adj_mode = t->adjacency;
+    // hub bitmaps serve the search variant: up to 1024 rows within 256 MB
     const int64_t row_bytes = ((n + 31) / 32) * 4;
     int64_t hubs = row_bytes > 0 ? (256ll << 20) / row_bytes : 0;
     if (hubs > 1024) hubs = 1024;
-    r.hub_count = static_cast<int>(hubs);
+    r.hub_count = r.adj_mode == kAdjSearch ? static_cast<int>(hubs) : 0;
     if (t) {
         if (t->block_size == 128 || t->block_size == 256 || t->block_size == 512 || t->block_size == 1024)
             r.block_size = t->block_size;
@@ -91,6 +93,14 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     if (l.gcap < 2) l.gcap = 2;
     l.hub_cap = t.hub_count;
     l.hub_words = (n + 31) / 32;
+    // edge hash set: a power-of-two number of 4-slot buckets, load <= 1/2
+    l.eset_buckets = 0;
+    if (t.adj_mode == kAdjHash) {
+        int64_t slots = 64;
+        while (slots < 2 * l.m_cap) slots <<= 1;
+        l.eset_buckets = slots / 4;
+    }
+    l.vtab_slots = t.adj_mode == kAdjVtab ? 2 * nnz : 0;
     l.radix_tiles = (n + kRadixTile - 1) / kRadixTile;
     if (l.radix_tiles < 1) l.radix_tiles = 1;
     int64_t scan_max = 256 * l.radix_tiles;
@@ -119,6 +129,8 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.gtau = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
     l.glam = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
     l.hub = take(static_cast<size_t>(l.hub_cap) * l.hub_words * sizeof(uint32_t));
+    l.eset = take(static_cast<size_t>(l.eset_buckets) * 4 * sizeof(uint64_t));
+    l.vtab = take(static_cast<size_t>(l.vtab_slots) * sizeof(int32_t));
     l.keys0 = take(n1 * sizeof(uint32_t));
     l.keys1 = take(n1 * sizeof(uint32_t));
     l.vals0 = take(n1 * sizeof(uint32_t));
@@ -218,6 +230,8 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
     g->gtau = reinterpret_cast<int32_t *>(ws + L.gtau);
     g->glam = reinterpret_cast<int32_t *>(ws + L.glam);
     g->hub = reinterpret_cast<uint32_t *>(ws + L.hub);
+    g->eset = L.eset_buckets ? reinterpret_cast<uint64_t *>(ws + L.eset) : nullptr;
+    g->vtab = L.vtab_slots ? reinterpret_cast<int32_t *>(ws + L.vtab) : nullptr;
     const int rc = load_graph(g, d_off, d_col, reinterpret_cast<cudaStream_t>(stream));
     if (rc != PS_OK) {
         delete g;

@@ -29,14 +29,19 @@ k_batch(const GraphDev *__restrict__ table, int32_t n_graphs, const ps_work *__r
         const ps_work w = s_w;
         Counts6 cnt;
         cnt.zero();
+        const int adj = s_g.adj_mode;
         if (w.sampler == 0) {
             if (s_g.W > 0)
                 for (uint32_t s = threadIdx.x; s < w.count; s += BLOCK)
-                    cnt.add(sample_3path(s_g, w.seed, w.first_id + s));
+                    cnt.add(adj == kAdjVtab   ? sample_3path<kAdjVtab>(s_g, w.seed, w.first_id + s)
+                            : adj == kAdjHash ? sample_3path<kAdjHash>(s_g, w.seed, w.first_id + s)
+                                              : sample_3path<kAdjSearch>(s_g, w.seed, w.first_id + s));
         } else {
             if (s_g.Lambda > 0)
                 for (uint32_t s = threadIdx.x; s < w.count; s += BLOCK)
-                    cnt.add(sample_centred(s_g, w.seed, w.first_id + s));
+                    cnt.add(adj == kAdjVtab   ? sample_centred<kAdjVtab>(s_g, w.seed, w.first_id + s)
+                            : adj == kAdjHash ? sample_centred<kAdjHash>(s_g, w.seed, w.first_id + s)
+                                              : sample_centred<kAdjSearch>(s_g, w.seed, w.first_id + s));
         }
         flush_counts<BLOCK>(cnt, w.sampler == 0 ? 6 : 4, hist + 6ull * w.slot);
     }

@@ -30,12 +30,20 @@ struct GraphDev {
     const int32_t *gtau;     // [Bt + 1] guide: first edge of each r >> tau_shift bucket
     const int32_t *glam;     // [Bl + 1]
     const uint32_t *hub;     // [hubs][hub_words] adjacency bitmaps of the top labels
+    const uint64_t *eset;    // hash set of the edges (4-slot buckets), or null
+    uint64_t eset_mask;      // buckets - 1
+    const int32_t *vtab;     // per-vertex hash tables: slots [2 off(x), 2 off(x+1)), or null
     uint64_t W, Lambda;
     int64_t n, m;
     int32_t hub_start;       // labels >= hub_start have a bitmap row
     int32_t hub_words;
     int32_t tau_shift, lam_shift;
+    int32_t adj_mode;        // kAdjHash or kAdjSearch
+    int32_t pad_;
 };
+
+// Adjacency test variants (chosen by the tuning; results are identical).
+enum { kAdjHash = 1, kAdjSearch = 2, kAdjVtab = 3 };
 
 // status block (uint64 words at the start of the workspace)
 enum {
@@ -228,6 +236,142 @@ __device__ __forceinline__ bool adjacent_known(const GraphDev &g, int32_t a, int
     }
     return in_sorted(g.col, oa, da, b);
 }
+
+// ----------------------------------------------------------- edge hash set
+
+// The hash-table adjacency that the O(1) test of Theorem 3.4 assumes: the
+// edges {a, b}, a < b, keyed (a << 32) | b, in buckets of four 8-byte slots
+// (32 bytes, one DRAM sector) with linear probing from bucket to bucket.
+// Slots only ever go from empty (all ones) to full, so a lookup that meets a
+// bucket with an empty slot before finding its key can stop: had the key
+// been inserted, it would sit in that bucket or an earlier one.
+constexpr uint64_t kEmptySlot = ~0ull;
+
+__device__ __forceinline__ uint64_t edge_key(int32_t a, int32_t b) {
+    return (static_cast<uint64_t>(static_cast<uint32_t>(a)) << 32) | static_cast<uint32_t>(b);
+}
+
+__device__ __forceinline__ uint64_t key_bucket(uint64_t key, uint64_t mask) {
+    uint64_t h = key * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xD6E8FEB86659FD93ull;
+    h ^= h >> 29;
+    return h & mask;
+}
+
+struct Bucket {
+    ulonglong2 lo, hi;
+};
+
+__device__ __forceinline__ Bucket load_bucket(const uint64_t *set, uint64_t b) {
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(set + (b << 2));
+    return Bucket{__ldg(p), __ldg(p + 1)};
+}
+
+// 1: key present, 0: absent, -1: bucket full without the key (probe on)
+__device__ __forceinline__ int bucket_verdict(const Bucket &k, uint64_t key) {
+    if (k.lo.x == key || k.lo.y == key || k.hi.x == key || k.hi.y == key) return 1;
+    if (k.lo.x == kEmptySlot || k.lo.y == kEmptySlot || k.hi.x == kEmptySlot || k.hi.y == kEmptySlot)
+        return 0;
+    return -1;
+}
+
+static __device__ __noinline__ bool probe_on(const uint64_t *set, uint64_t mask, uint64_t key,
+                                             uint64_t b) {
+    for (uint64_t i = 0; i < mask; i++) {
+        b = (b + 1) & mask;
+        const int v = bucket_verdict(load_bucket(set, b), key);
+        if (v >= 0) return v == 1;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool eset_contains(const uint64_t *set, uint64_t mask, int32_t x, int32_t y) {
+    if (x == y) return false;
+    const uint64_t key = edge_key(min(x, y), max(x, y));
+    const uint64_t b = key_bucket(key, mask);
+    const int v = bucket_verdict(load_bucket(set, b), key);
+    return v >= 0 ? v == 1 : probe_on(set, mask, key, b);
+}
+
+// Two independent lookups (x != y for both) with their first buckets loaded together.
+__device__ __forceinline__ void eset_contains2(const uint64_t *set, uint64_t mask, int32_t x0,
+                                               int32_t y0, int32_t x1, int32_t y1, bool &r0, bool &r1) {
+    const uint64_t k0 = edge_key(min(x0, y0), max(x0, y0));
+    const uint64_t k1 = edge_key(min(x1, y1), max(x1, y1));
+    const uint64_t b0 = key_bucket(k0, mask), b1 = key_bucket(k1, mask);
+    const Bucket q0 = load_bucket(set, b0), q1 = load_bucket(set, b1);
+    const int v0 = bucket_verdict(q0, k0), v1 = bucket_verdict(q1, k1);
+    r0 = v0 >= 0 ? v0 == 1 : probe_on(set, mask, k0, b0);
+    r1 = v1 >= 0 ? v1 == 1 : probe_on(set, mask, k1, b1);
+}
+
+// Three independent lookups with their first buckets loaded together.
+__device__ __forceinline__ void eset_contains3(const uint64_t *set, uint64_t mask, int32_t x0,
+                                               int32_t y0, int32_t x1, int32_t y1, int32_t x2,
+                                               int32_t y2, bool &r0, bool &r1, bool &r2) {
+    const uint64_t k0 = edge_key(min(x0, y0), max(x0, y0));
+    const uint64_t k1 = edge_key(min(x1, y1), max(x1, y1));
+    const uint64_t k2 = edge_key(min(x2, y2), max(x2, y2));
+    const uint64_t b0 = key_bucket(k0, mask), b1 = key_bucket(k1, mask), b2 = key_bucket(k2, mask);
+    const Bucket q0 = load_bucket(set, b0), q1 = load_bucket(set, b1), q2 = load_bucket(set, b2);
+    const int v0 = bucket_verdict(q0, k0), v1 = bucket_verdict(q1, k1), v2 = bucket_verdict(q2, k2);
+    r0 = (x0 != y0) && (v0 >= 0 ? v0 == 1 : probe_on(set, mask, k0, b0));
+    r1 = (x1 != y1) && (v1 >= 0 ? v1 == 1 : probe_on(set, mask, k1, b1));
+    r2 = (x2 != y2) && (v2 >= 0 ? v2 == 1 : probe_on(set, mask, k2, b2));
+}
+
+// ------------------------------------------------ per-vertex hash tables
+
+// Each adjacency list in its own open-addressing table (Theorem 3.4 assumes
+// hash-table adjacency lists): the table of vertex x is the 2 d_x int32
+// slots starting at 2 off(x), holding the neighbours of x (empty = -1),
+// linear probing with wrap-around inside the table.  The slot of y is
+// (mix(y) * 2 d_x) >> 32.  Lookups go to the table of the endpoint that is a
+// sampled edge's endpoint or else the larger label, so they concentrate on
+// the tables of high-degree vertices, which stay in L2.
+constexpr int32_t kEmptyLabel = -1;
+
+__device__ __forceinline__ uint32_t label_mix(int32_t y) {
+    uint32_t h = static_cast<uint32_t>(y) * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    return h;
+}
+
+__device__ __forceinline__ uint64_t vtab_start(int32_t y, uint64_t size) {
+    return (static_cast<uint64_t>(label_mix(y)) * size) >> 32;
+}
+
+static __device__ __noinline__ bool vtab_probe_on(const int32_t *t, uint64_t size, int32_t y, uint64_t s) {
+    for (uint64_t i = 1; i < size; i++) {
+        s = (s + 1 == size) ? 0 : s + 1;
+        const int32_t x = __ldg(t + s);
+        if (x == y) return true;
+        if (x == kEmptyLabel) return false;
+    }
+    return false;
+}
+
+// Is y a neighbour of the vertex whose row is [off, off + d)?
+struct VtabQuery {
+    const int32_t *t;
+    uint64_t size, s;
+    int32_t y;
+    __device__ __forceinline__ void start(const int32_t *vtab, int64_t off, int64_t d, int32_t key) {
+        t = vtab + 2 * off;
+        size = static_cast<uint64_t>(2 * d);
+        y = key;
+        s = size ? vtab_start(key, size) : 0;
+    }
+    __device__ __forceinline__ int32_t first() const { return size ? __ldg(t + s) : kEmptyLabel; }
+    __device__ __forceinline__ bool resolve(int32_t x) const {
+        if (x == y) return true;
+        if (x == kEmptyLabel) return false;
+        return vtab_probe_on(t, size, y, s);
+    }
+};
 
 // ------------------------------------------------------------- warp utils
 

@@ -14,7 +14,7 @@ namespace ps {
 // Sort tiers of the row relabel-and-sort step, by row length.
 constexpr int kTierA = 32;      // one warp, registers
 constexpr int kTierB = 1024;    // one warp, shared memory
-constexpr int kTierC = 32768;   // one block, shared memory (128 KB)
+constexpr int kTierC = 4096;    // one block, shared memory (16 KB); above: block radix sort
 // Hub rows are only worth a bitmap above this degree.
 constexpr int kHubMinDegree = 64;
 // Items per tile of every scan.
@@ -32,12 +32,15 @@ struct Tuning {
     int guide_log2_ratio;  // -1: no guide
     int hub_count;         // 0: none
     int samples_per_thread;
+    int adj_mode;          // kAdjHash or kAdjSearch
 };
 Tuning resolve_tuning(const ps_tuning *t, int64_t n);
 
 struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
-    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub;
+    int64_t eset_buckets;  // 0 without the edge hash set
+    int64_t vtab_slots;    // 0 without the per-vertex tables
+    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab;
     size_t keys0, keys1, vals0, vals1, rcounts, scan_flag, scan_agg, scan_inc;
     size_t total;
 };
@@ -64,6 +67,8 @@ struct ps_graph {
     uint64_t *ptau, *plam;
     int32_t *gtau, *glam;
     uint32_t *hub;
+    uint64_t *eset;
+    int32_t *vtab;
     bool prefixed;
     ps_stats stats;
     ps::GraphDev dev;

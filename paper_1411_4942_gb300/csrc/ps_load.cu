@@ -301,8 +301,9 @@ __global__ void __launch_bounds__(256) k_sort_tier_b(RowIn R) {
     report(R, bad, nsimple);
 }
 
-// Tier C: rows of 1025..32768 entries, one block of 1024, shared-memory bitonic.
-__global__ void __launch_bounds__(1024) k_sort_tier_c(RowIn R) {
+// Tier C: rows of 1025..4096 entries, one block of 512, shared-memory bitonic
+// (16 KB, several blocks per SM).
+__global__ void __launch_bounds__(512) k_sort_tier_c(RowIn R) {
     extern __shared__ int32_t s_dyn[];
     __shared__ int s_low;
     const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 2]);
@@ -349,11 +350,14 @@ __global__ void __launch_bounds__(1024) k_sort_tier_c(RowIn R) {
     report(R, bad, nsimple);
 }
 
-// Tier D: rows above 32768 entries, one block of 1024, stable LSD radix sort
-// (8-bit digits) ping-ponging between the output row and a scratch row.
+// Tier D: rows above 4096 entries, one block of 1024, stable LSD radix sort
+// (8-bit digits) ping-ponging between the output row and a scratch row.  Each
+// pass is a warp-level multisplit: every warp owns a contiguous slice of the
+// row, counts its digits, gets per-(digit, warp) offsets from one block-wide
+// scan, and scatters its slice in order -- stable without block barriers
+// inside the scatter.
 __global__ void __launch_bounds__(1024) k_sort_tier_d(RowIn R, int32_t *tmp, int bits) {
-    __shared__ uint32_t s_hist[256];
-    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tot[256];
     __shared__ uint32_t s_wcnt[32][256];
     __shared__ int s_low;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -361,8 +365,6 @@ __global__ void __launch_bounds__(1024) k_sort_tier_d(RowIn R, int32_t *tmp, int
     const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 4]);
     const int64_t tbase = (r0 < r1) ? R.coff[r0] : 0;
     bool bad = false, nsimple = false;
-    for (int w = 0; w < 32; w++)
-        if (threadIdx.x < 256) s_wcnt[w][threadIdx.x] = 0;
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const uint32_t v = R.inv[r];
         const int64_t o = ldg_i64(R.off + v);
@@ -373,17 +375,30 @@ __global__ void __launch_bounds__(1024) k_sort_tier_d(RowIn R, int32_t *tmp, int
             scr[i] = relabel(R, o + i, v, (int32_t)r, bad, nsimple);
         __syncthreads();
         int32_t *src = scr, *dst = out;
+        const int64_t slice = (d + 31) / 32;
+        const int64_t lo = warp * slice;
+        const int64_t hi = (lo + slice < d) ? lo + slice : d;
         for (int shift = 0; shift < bits; shift += 8) {
-            if (threadIdx.x < 256) s_hist[threadIdx.x] = 0;
+            // (1) per-warp digit counts of the warp's slice
+            if (threadIdx.x < 256)
+                for (int w = 0; w < 32; w++) s_wcnt[w][threadIdx.x] = 0;
             __syncthreads();
-            for (int64_t i = threadIdx.x; i < d; i += blockDim.x)
-                atomicAdd(&s_hist[(static_cast<uint32_t>(src[i]) >> shift) & 255u], 1u);
+            for (int64_t i = lo + lane; i < hi; i += 32)
+                atomicAdd(&s_wcnt[warp][(static_cast<uint32_t>(src[i]) >> shift) & 255u], 1u);
+            __syncthreads();
+            // (2) offsets in (digit, warp) order: digit totals, their
+            // exclusive scan, then the warps in order within each digit
+            if (threadIdx.x < 256) {
+                uint32_t t = 0;
+                for (int w = 0; w < 32; w++) t += s_wcnt[w][threadIdx.x];
+                s_tot[threadIdx.x] = t;
+            }
             __syncthreads();
             if (warp == 0) {
                 uint32_t h[8], run = 0;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    h[q] = s_hist[lane * 8 + q];
+                    h[q] = s_tot[lane * 8 + q];
                     run += h[q];
                 }
                 uint32_t x = run;
@@ -395,36 +410,37 @@ __global__ void __launch_bounds__(1024) k_sort_tier_d(RowIn R, int32_t *tmp, int
                 uint32_t e = x - run;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    s_base[lane * 8 + q] = e;
+                    s_tot[lane * 8 + q] = e;
                     e += h[q];
                 }
             }
             __syncthreads();
-            for (int64_t i0 = 0; i0 < d; i0 += blockDim.x) {
-                const int64_t i = i0 + threadIdx.x;
-                const bool valid = i < d;
+            if (threadIdx.x < 256) {
+                uint32_t base = s_tot[threadIdx.x];
+                for (int w = 0; w < 32; w++) {
+                    const uint32_t c = s_wcnt[w][threadIdx.x];
+                    s_wcnt[w][threadIdx.x] = base;
+                    base += c;
+                }
+            }
+            __syncthreads();
+            // (3) each warp scatters its slice in order
+            for (int64_t i0 = lo; i0 < hi; i0 += 32) {
+                const int64_t i = i0 + lane;
+                const bool valid = i < hi;
                 const int32_t x = valid ? src[i] : 0;
                 const uint32_t digit = valid ? ((static_cast<uint32_t>(x) >> shift) & 255u) : 256u;
                 const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-                const uint32_t wrank = __popc(peers & lanemask_lt());
-                if (valid && lane == __ffs(peers) - 1) s_wcnt[warp][digit] = __popc(peers);
-                __syncthreads();
+                const uint32_t rank = __popc(peers & lanemask_lt());
+                const uint32_t base = valid ? s_wcnt[warp][digit] : 0u;
+                __syncwarp();
                 if (valid) {
-                    uint32_t pos = s_base[digit] + wrank;
-                    for (int w = 0; w < warp; w++) pos += s_wcnt[w][digit];
-                    dst[pos] = x;
+                    dst[base + rank] = x;
+                    if (lane == __ffs(peers) - 1) s_wcnt[warp][digit] = base + __popc(peers);
                 }
-                __syncthreads();
-                if (threadIdx.x < 256) {
-                    uint32_t tot = 0;
-                    for (int w = 0; w < 32; w++) {
-                        tot += s_wcnt[w][threadIdx.x];
-                        s_wcnt[w][threadIdx.x] = 0;
-                    }
-                    s_base[threadIdx.x] += tot;
-                }
-                __syncthreads();
+                __syncwarp();
             }
+            __syncthreads();
             int32_t *t = src;
             src = dst;
             dst = t;
@@ -472,9 +488,10 @@ struct StoreUbase {
 };
 
 // Edge j = (u, v), u < v, in row-major order: j = ubase[u] + (iu - lowcnt[u]).
-// Upper arcs (u -> v) fill u, v, d_u, d_v, iu, off_u, off_v; lower arcs
-// (v -> u, at position jv of N(v)) find v in the upper part of N(u) and fill
-// jv.  A lower arc without its upper partner means an asymmetric input.
+// Each lower arc (v -> u, at position jv of N(v)) finds v in the upper part
+// of N(u) -- the shorter list, since u precedes v -- and writes the whole
+// record of its edge.  A lower arc without its upper partner means an
+// asymmetric input.
 constexpr int kEdgeItems = 8;
 __global__ void __launch_bounds__(256)
 k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
@@ -499,43 +516,32 @@ k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t 
                 r++;
                 rend = ldg_i64(coff + r + 1);
             }
+            const int32_t x = ldg_i32(ccol + i);
+            if (x >= r) continue;  // upper arcs are written from the other side
             const int64_t ro = ldg_i64(coff + r);
             const int32_t p = static_cast<int32_t>(i - ro);
-            const int32_t x = ldg_i32(ccol + i);
-            if (x > r) {
-                const int64_t j = ldg_i64(ubase + r) + p - ldg_i32(lowcnt + r);
-                if (j < 0 || j >= m_cap) {
-                    asym = true;
-                    continue;
-                }
-                const int64_t ox = ldg_i64(coff + x);
-                const int64_t dx = ldg_i64(coff + x + 1) - ox;
-                int32_t *e = reinterpret_cast<int32_t *>(rec + j);
-                *reinterpret_cast<int4 *>(e) =
-                    make_int4((int32_t)r, x, (int32_t)(rend - ro), (int32_t)dx);
-                e[4] = p;
-                *reinterpret_cast<int2 *>(e + 6) = make_int2((int32_t)ro, (int32_t)ox);
-            } else if (x < r) {
-                const int64_t ox = ldg_i64(coff + x);
-                const int32_t lx = ldg_i32(lowcnt + x);
-                const int64_t dx = ldg_i64(coff + x + 1) - ox;
-                int64_t a = ox + lx, b = ox + dx;  // lower_bound of r in the upper part
-                while (a < b) {
-                    const int64_t mid = (a + b) >> 1;
-                    if (ldg_i32(ccol + mid) < r) a = mid + 1;
-                    else b = mid;
-                }
-                if (a >= ox + dx || ldg_i32(ccol + a) != (int32_t)r) {
-                    asym = true;
-                    continue;
-                }
-                const int64_t j = ldg_i64(ubase + x) + (a - ox - lx);
-                if (j < 0 || j >= m_cap) {
-                    asym = true;
-                    continue;
-                }
-                reinterpret_cast<int32_t *>(rec + j)[5] = p;
+            const int64_t ox = ldg_i64(coff + x);
+            const int32_t lx = ldg_i32(lowcnt + x);
+            const int64_t dx = ldg_i64(coff + x + 1) - ox;
+            int64_t a = ox + lx, b = ox + dx;  // lower_bound of r in the upper part
+            while (a < b) {
+                const int64_t mid = (a + b) >> 1;
+                if (ldg_i32(ccol + mid) < r) a = mid + 1;
+                else b = mid;
             }
+            if (a >= ox + dx || ldg_i32(ccol + a) != (int32_t)r) {
+                asym = true;
+                continue;
+            }
+            const int32_t iu = static_cast<int32_t>(a - ox);
+            const int64_t j = ldg_i64(ubase + x) + (iu - lx);
+            if (j < 0 || j >= m_cap) {
+                asym = true;
+                continue;
+            }
+            int4 *e = reinterpret_cast<int4 *>(rec + j);
+            e[0] = make_int4(x, (int32_t)r, (int32_t)dx, (int32_t)(rend - ro));
+            e[1] = make_int4(iu, p, (int32_t)ox, (int32_t)ro);
         }
     }
     if (asym) raise_flag(status, F_ASYM);
@@ -606,14 +612,13 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         PS_LAUNCH_CHECK();
         if (g->d_max > kTierB) {
             const int smem = kTierC * (int)sizeof(int32_t);
-            PS_CUDA_TRY(cudaFuncSetAttribute(k_sort_tier_c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            k_sort_tier_c<<<sms, 1024, smem, s>>>(R);
+            k_sort_tier_c<<<sms * 4, 512, smem, s>>>(R);
             PS_LAUNCH_CHECK();
         }
         if (g->d_max > kTierC) {
             int vb = 0;
             while (vb < 31 && (static_cast<uint64_t>(n - 1) >> vb) != 0) vb++;
-            k_sort_tier_d<<<sms, 1024, 0, s>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
+            k_sort_tier_d<<<sms * 2, 1024, 0, s>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
             PS_LAUNCH_CHECK();
         }
     }

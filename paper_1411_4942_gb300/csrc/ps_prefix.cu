@@ -19,11 +19,21 @@ struct LoadWeights {
     const EdgeRec *rec;
     __device__ U64x2 operator()(int64_t j) const { return weights(ldg_rec(rec + j)); }
 };
+// The weights are non-negative, so a running sum that passes 2^64 shows up at
+// the first item whose inclusive prefix is below its exclusive one; the last
+// item's prefixes are W and Lambda.
 struct StorePrefix {
     uint64_t *ptau, *plam;
-    __device__ void operator()(int64_t j, U64x2, U64x2 inc) const {
+    u64 *status;
+    int64_t m;
+    __device__ void operator()(int64_t j, U64x2 exc, U64x2 inc) const {
         ptau[j] = inc.a;
         plam[j] = inc.b;
+        if (inc.a < exc.a || inc.b < exc.b) raise_flag(status, F_OVERFLOW);
+        if (j == m - 1) {
+            status[ST_W_LO] = inc.a;
+            status[ST_L_LO] = inc.b;
+        }
     }
 };
 
@@ -46,24 +56,6 @@ __device__ __forceinline__ void warp_add128(uint64_t &lo, uint64_t &hi) {
         const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
         add128(lo, hi, l2);
         hi += h2;
-    }
-}
-
-// 128-bit sums of tau and lambda (W and Lambda must fit in 64 bits for the
-// prefixes to be exact).
-__global__ void __launch_bounds__(256) k_weight_totals(int64_t m, const EdgeRec *__restrict__ rec, u64 *status) {
-    uint64_t wl = 0, wh = 0, ll = 0, lh = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const U64x2 w = weights(ldg_rec(rec + j));
-        add128(wl, wh, w.a);
-        add128(ll, lh, w.b);
-    }
-    warp_add128(wl, wh);
-    warp_add128(ll, lh);
-    if ((threadIdx.x & 31) == 0) {
-        if (wl | wh) atomic_add128(status + ST_W_LO, wl, wh);
-        if (ll | lh) atomic_add128(status + ST_L_LO, ll, lh);
     }
 }
 
@@ -100,35 +92,42 @@ k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, u6
     }
 }
 
-// Guide table: bucket b holds r in [b << shift, (b + 1) << shift).  Edge j
-// covers r in [P[j-1], P[j] - 1]; it marks the first bucket that starts in
-// its range, and an inclusive max-scan carries the mark over the following
-// buckets, so G[b] = the edge that the first r of bucket b selects.
-__global__ void k_guide_marks(int64_t m, const uint64_t *__restrict__ P, int shift, int32_t *G) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const uint64_t prev = j ? P[j - 1] : 0ull;
-        const uint64_t cur = P[j];
-        if (cur == prev) continue;
-        const uint64_t bstart = prev ? ((prev - 1) >> shift) + 1 : 0ull;
-        const uint64_t bend = (cur - 1) >> shift;
-        if (bstart <= bend) G[bstart] = static_cast<int32_t>(j);
+// Guide table: bucket b holds r in [b << shift, (b + 1) << shift), and G[b]
+// is the edge that the first r of bucket b selects.  Edge j covers r in
+// [P[j-1], P[j] - 1], so it owns the buckets whose first r falls in that
+// range -- a contiguous run, and every bucket has exactly one owner.  Each
+// lane writes its own short run; a warp writes long runs together.
+__global__ void __launch_bounds__(256)
+k_guide_fill(int64_t m, const uint64_t *__restrict__ P, int shift, int32_t *G, int64_t B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    if (blockIdx.x == 0 && threadIdx.x == 0) G[B] = static_cast<int32_t>(m - 1);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w * 32 < m; w += nw) {
+        const int64_t j = w * 32 + lane;
+        uint64_t bstart = 0, len = 0;
+        if (j < m) {
+            const uint64_t prev = j ? P[j - 1] : 0ull;
+            const uint64_t cur = P[j];
+            if (cur != prev) {
+                bstart = prev ? ((prev - 1) >> shift) + 1 : 0ull;
+                const uint64_t bend = (cur - 1) >> shift;
+                len = bstart <= bend ? bend - bstart + 1 : 0;
+            }
+        }
+        if (len <= 8) {
+            for (uint64_t q = 0; q < len; q++) G[bstart + q] = static_cast<int32_t>(j);
+        }
+        uint32_t longs = __ballot_sync(0xffffffffu, len > 8);
+        while (longs) {
+            const int l = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const uint64_t bs = __shfl_sync(0xffffffffu, bstart, l);
+            const uint64_t ln = __shfl_sync(0xffffffffu, len, l);
+            const int32_t jj = static_cast<int32_t>(w * 32 + l);
+            for (uint64_t q = lane; q < ln; q += 32) G[bs + q] = jj;
+        }
     }
 }
-
-struct LoadI32 {
-    const int32_t *p;
-    __device__ int32_t operator()(int64_t i) const { return p[i]; }
-};
-struct StoreGuide {
-    int32_t *G;
-    int64_t B;
-    int32_t last;
-    __device__ void operator()(int64_t i, int32_t, int32_t inc) const {
-        G[i] = inc;
-        if (i == B - 1) G[B] = last;
-    }
-};
 
 // One warp per hub row: set bit x of row h for every neighbour x.
 __global__ void __launch_bounds__(256)
@@ -146,6 +145,78 @@ k_hub_bits(int64_t hub_start, int64_t n, const int64_t *__restrict__ coff, const
     }
 }
 
+// Inserts every edge (u < v) into the hash set; slots are claimed with
+// compare-and-swap, so the set's contents (not its layout) are deterministic.
+__global__ void __launch_bounds__(256)
+k_eset_build(int64_t m, const EdgeRec *__restrict__ rec, uint64_t *set, uint64_t mask, u64 *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool failed = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int2 uv = __ldg(reinterpret_cast<const int2 *>(rec + j));
+        const uint64_t key = edge_key(uv.x, uv.y);
+        uint64_t b = key_bucket(key, mask);
+        bool done = false;
+        for (uint64_t probe = 0; probe <= mask && !done; probe++) {
+            unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + (b << 2));
+            for (int s = 0; s < 4; s++) {
+                const unsigned long long old = atomicCAS(slot + s, kEmptySlot, key);
+                if (old == kEmptySlot || old == key) {
+                    done = true;
+                    break;
+                }
+            }
+            b = (b + 1) & mask;
+        }
+        failed |= !done;
+    }
+    if (failed) raise_flag(status, F_OVERFLOW);
+}
+
+// Inserts every arc (x -> y) into the table of x with compare-and-swap; the
+// tables' contents are deterministic, their slot layout is not.
+constexpr int kVtabItems = 8;
+__global__ void __launch_bounds__(256)
+k_vtab_build(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+             int32_t *vtab, u64 *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool failed = false;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c * kVtabItems < nnz; c += stride) {
+        const int64_t i0 = c * kVtabItems;
+        int64_t lo = 0, hi = n;  // last row r with coff[r] <= i0
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (ldg_i64(coff + mid) <= i0) lo = mid;
+            else hi = mid - 1;
+        }
+        int64_t r = lo;
+        int64_t ro = ldg_i64(coff + r), rend = ldg_i64(coff + r + 1);
+        for (int t = 0; t < kVtabItems; t++) {
+            const int64_t i = i0 + t;
+            if (i >= nnz) break;
+            while (rend <= i) {
+                r++;
+                ro = rend;
+                rend = ldg_i64(coff + r + 1);
+            }
+            const int32_t y = ldg_i32(ccol + i);
+            const uint64_t size = static_cast<uint64_t>(2 * (rend - ro));
+            int32_t *tab = vtab + 2 * ro;
+            uint64_t s = vtab_start(y, size);
+            bool done = false;
+            for (uint64_t probe = 0; probe < size; probe++) {
+                const int32_t old = atomicCAS(tab + s, kEmptyLabel, y);
+                if (old == kEmptyLabel || old == y) {
+                    done = true;
+                    break;
+                }
+                s = (s + 1 == size) ? 0 : s + 1;
+            }
+            failed |= !done;
+        }
+    }
+    if (failed) raise_flag(status, F_OVERFLOW);
+}
+
 static int guide_shift(uint64_t W, int64_t gcap) {
     int s = 0;
     while (s < 63 && (((W - 1) >> s) + 1) > static_cast<uint64_t>(gcap)) s++;
@@ -158,17 +229,10 @@ static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *
     const int shift = guide_shift(total, g->L.gcap);
     const int64_t B = static_cast<int64_t>(((total - 1) >> shift) + 1);
     *shift_out = shift;
-    PS_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(int32_t) * (B + 1), s));
+    (void)slot;
     int64_t blocks = (m + 255) / 256;
     if (blocks > (int64_t)g->sm_count * 32) blocks = (int64_t)g->sm_count * 32;
-    k_guide_marks<<<(unsigned)blocks, 256, 0, s>>>(m, P, shift, G);
-    PS_LAUNCH_CHECK();
-    int rc = reset_scan(g, slot, B, s);
-    if (rc) return rc;
-    const int64_t tiles = (B + kScanTile - 1) / kScanTile;
-    k_scan<int32_t, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
-        B, scan_state<int32_t>(g, slot), (int32_t)0, OpMax(), LoadI32{G},
-        StoreGuide{G, B, static_cast<int32_t>(m - 1)});
+    k_guide_fill<<<(unsigned)blocks, 256, 0, s>>>(m, P, shift, G, B);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }
@@ -183,9 +247,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         const int64_t tiles = (m + kScanTile - 1) / kScanTile;
         k_scan<U64x2, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
             m, scan_state<U64x2>(g, 3), U64x2{0, 0}, OpSum(), LoadWeights{g->rec},
-            StorePrefix{g->ptau, g->plam});
-        PS_LAUNCH_CHECK();
-        k_weight_totals<<<sms * 8, 256, 0, s>>>(m, g->rec, g->status);
+            StorePrefix{g->ptau, g->plam, g->status, m});
         PS_LAUNCH_CHECK();
     }
     if (n > 0) {
@@ -204,8 +266,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     S.n = n;
     S.m = m;
     S.d_max = g->d_max;
-    const bool overflow = st[ST_W_HI] != 0 || st[ST_L_HI] != 0;
-    if (overflow) return PS_ERR_OVERFLOW;
+    if (st[ST_FLAGS] & F_OVERFLOW) return PS_ERR_OVERFLOW;
 
     // guide tables (with guides off the table has at most 2 buckets)
     int tshift = 0, lshift = 0;
@@ -220,6 +281,30 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     S.tau_shift = tshift;
     S.lambda_shift = lshift;
 
+    // edge hash set
+    const uint64_t eset_mask = g->L.eset_buckets > 0 ? static_cast<uint64_t>(g->L.eset_buckets - 1) : 0;
+    if (g->eset) {
+        PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * 4 * g->L.eset_buckets, s));
+        if (m > 0) {
+            int64_t blocks = (m + 255) / 256;
+            if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
+            k_eset_build<<<(unsigned)blocks, 256, 0, s>>>(m, g->rec, g->eset, eset_mask, g->status);
+            PS_LAUNCH_CHECK();
+        }
+    }
+
+    // per-vertex hash tables
+    if (g->vtab) {
+        PS_CUDA_TRY(cudaMemsetAsync(g->vtab, 0xFF, sizeof(int32_t) * g->L.vtab_slots, s));
+        if (g->nnz > 0) {
+            int64_t chunks = (g->nnz + kVtabItems - 1) / kVtabItems;
+            int64_t blocks = (chunks + 255) / 256;
+            if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
+            k_vtab_build<<<(unsigned)blocks, 256, 0, s>>>(n, g->nnz, g->off, g->col, g->vtab, g->status);
+            PS_LAUNCH_CHECK();
+        }
+    }
+
     // hub bitmaps
     const int64_t hubs = static_cast<int64_t>(st[ST_HUBS]);
     S.hubs = hubs;
@@ -230,11 +315,16 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         k_hub_bits<<<(unsigned)blocks, 256, 0, s>>>(n - hubs, n, g->off, g->col, g->hub, g->L.hub_words);
         PS_LAUNCH_CHECK();
     }
-    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
-    PS_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st[ST_FLAGS] & F_TIMEOUT) return PS_ERR_TIMEOUT;
+    // The kernels queued after the synchronisation cannot fail on valid
+    // state (the hash set's load is at most 1/2, so every insertion finds a
+    // slot); later calls on `stream` are ordered after them.
 
     GraphDev &D = g->dev;
+    D.eset = g->eset;
+    D.eset_mask = eset_mask;
+    D.vtab = g->vtab;
+    D.adj_mode = g->vtab ? kAdjVtab : (g->eset ? kAdjHash : kAdjSearch);
+    D.pad_ = 0;
     D.off = g->off;
     D.col = g->col;
     D.rec = g->rec;

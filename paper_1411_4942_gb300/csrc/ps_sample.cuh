@@ -13,6 +13,7 @@ namespace ps {
 
 // Class of one Alg. 1 output: 0 = triangle (u' == v'), 1 = 3-path,
 // 2 = tailed triangle, 3 = 4-cycle, 4 = chordal 4-cycle, 5 = 4-clique.
+template <int ADJ>
 __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, uint64_t id) {
     const uint4 w = sample_block(seed, id, 0, 0);
     uint64_t r;
@@ -30,9 +31,28 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     const int32_t vp = ldg_i32(g.col + e.ov + pb);
     if (up == vp) return 0;
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
-    const bool e1 = (up < e.v) ? adjacent(g, up, e.v) : adjacent_known(g, e.v, e.ov, e.dv, up);
-    const bool e2 = (e.u < vp) ? adjacent_known(g, e.u, e.ou, e.du, vp) : adjacent(g, vp, e.u);
-    const bool e3 = adjacent(g, up, vp);
+    bool e1, e2, e3;
+    if (ADJ == kAdjHash) {
+        eset_contains3(g.eset, g.eset_mask, up, e.v, e.u, vp, up, vp, e1, e2, e3);
+    } else if (ADJ == kAdjVtab) {
+        // (u', v) in the table of v, (u, v') in the table of u -- both rows
+        // are in the edge record -- and (u', v') in the larger label's table
+        const int32_t x3 = max(up, vp);
+        const int64_t o3 = ldg_i64(g.off + x3);
+        const int64_t d3 = ldg_i64(g.off + x3 + 1) - o3;
+        VtabQuery q1, q2, q3;
+        q1.start(g.vtab, e.ov, e.dv, up);
+        q2.start(g.vtab, e.ou, e.du, vp);
+        q3.start(g.vtab, o3, d3, min(up, vp));
+        const int32_t f1 = q1.first(), f2 = q2.first(), f3 = q3.first();
+        e1 = q1.resolve(f1);
+        e2 = q2.resolve(f2);
+        e3 = q3.resolve(f3);
+    } else {
+        e1 = (up < e.v) ? adjacent(g, up, e.v) : adjacent_known(g, e.v, e.ov, e.dv, up);
+        e2 = (e.u < vp) ? adjacent_known(g, e.u, e.ou, e.du, vp) : adjacent(g, vp, e.u);
+        e3 = adjacent(g, up, vp);
+    }
     const int s = (int)e1 + (int)e2 + (int)e3;
     return s == 0 ? 1 : (s == 1 ? (e3 ? 3 : 2) : (s == 2 ? 4 : 5));
 }
@@ -41,6 +61,7 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
 // 4-cycle, 3 = 4-clique.  u' is drawn among the L_{u,v} entries of N(u)
 // after v, v' among the L_{v,u} entries of N(v) after u; the path is centred
 // (Definition 4.1) iff (u', v') is an edge.
+template <int ADJ>
 __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, uint64_t id) {
     const uint4 w = sample_block(seed, id, 0, 1);
     uint64_t r;
@@ -55,6 +76,29 @@ __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, 
     if (!lemire32(w.w, lv, b)) b = draw_small_retry(seed, id, 1, 3, lv);
     const int32_t up = ldg_i32(g.col + e.ou + e.iu + 1 + static_cast<int32_t>(a));
     const int32_t vp = ldg_i32(g.col + e.ov + e.jv + 1 + static_cast<int32_t>(b));
+    if (ADJ == kAdjVtab) {
+        if (up == vp) return 0;
+        // the chords (u', v) and (u, v') in the tables of v and u (rows known
+        // from the record, looked up alongside), the closing edge (u', v') in
+        // the larger label's table
+        const int32_t x = max(up, vp);
+        const int64_t ox = ldg_i64(g.off + x);
+        const int64_t dx = ldg_i64(g.off + x + 1) - ox;
+        VtabQuery q0, q1, q2;
+        q1.start(g.vtab, e.ov, e.dv, up);
+        q2.start(g.vtab, e.ou, e.du, vp);
+        q0.start(g.vtab, ox, dx, min(up, vp));
+        const int32_t f1 = q1.first(), f2 = q2.first(), f0 = q0.first();
+        if (!q0.resolve(f0)) return 0;  // not centred
+        return 1 + (int)q1.resolve(f1) + (int)q2.resolve(f2);
+    }
+    if (ADJ == kAdjHash) {
+        // the closing edge first; the two chords only for centred paths
+        if (!eset_contains(g.eset, g.eset_mask, up, vp)) return 0;  // also u' == v'
+        bool c1, c2;
+        eset_contains2(g.eset, g.eset_mask, e.v, up, e.u, vp, c1, c2);
+        return 1 + (int)c1 + (int)c2;
+    }
     if (!adjacent(g, up, vp)) return 0;  // also covers u' == v'
     // u' > v and v' > u in label order, so the chord tests search N(v) and N(u)
     const bool c1 = adjacent_known(g, e.v, e.ov, e.dv, up);

@@ -41,7 +41,8 @@ class PathSampleError(RuntimeError):
 class PsTuning(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("guide_log2_ratio", ctypes.c_int32), ("hub_count", ctypes.c_int32),
-                ("samples_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("samples_per_thread", ctypes.c_int32), ("adjacency", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PsStats(ctypes.Structure):
@@ -249,10 +250,15 @@ def ps_batch_sample(handles, d_items, n_items, d_hist, d_table, d_counter, tunin
                                               d_counter, _tuning_ptr(tuning), _stream_ptr(stream)))
 
 
-def make_tuning(block_size=0, blocks_per_sm=0, guide_log2_ratio=0, hub_count=0) -> PsTuning:
+ADJ_HASH, ADJ_SEARCH, ADJ_VTAB = 1, 2, 3
+
+
+def make_tuning(block_size=0, blocks_per_sm=0, guide_log2_ratio=0, hub_count=0,
+                adjacency=0) -> PsTuning:
     t = PsTuning()
     t.block_size, t.blocks_per_sm = block_size, blocks_per_sm
     t.guide_log2_ratio, t.hub_count = guide_log2_ratio, hub_count
+    t.adjacency = adjacency
     return t
 
 

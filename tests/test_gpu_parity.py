@@ -197,7 +197,13 @@ def test_tunings_do_not_change_results():
     ref4 = O.sample_centered(og, 300007, 99, 5, threads=8)
     for t in (None, ps.make_tuning(block_size=128, guide_log2_ratio=-1, hub_count=-1),
               ps.make_tuning(block_size=512, blocks_per_sm=1, guide_log2_ratio=4, hub_count=2000),
-              ps.make_tuning(block_size=1024, hub_count=5)):
+              ps.make_tuning(block_size=1024, hub_count=5),
+              ps.make_tuning(adjacency=ps.ADJ_SEARCH),
+              ps.make_tuning(block_size=128, guide_log2_ratio=1, adjacency=ps.ADJ_SEARCH,
+                             hub_count=-1),
+              ps.make_tuning(block_size=512, adjacency=ps.ADJ_SEARCH, hub_count=3000),
+              ps.make_tuning(adjacency=ps.ADJ_VTAB),
+              ps.make_tuning(block_size=128, guide_log2_ratio=2, adjacency=ps.ADJ_VTAB)):
         G = _load(g, t)
         h6, h4 = _hists(G, 300007, 300007, 99, 5)
         assert h6.tolist() == ref6.tolist() and h4.tolist() == ref4.tolist()
