@@ -1,0 +1,104 @@
+"""Batched launch and serving loop on the GPU: every request's class counts
+must equal those of the same request run alone with the plain calls (integer
+counts, so bit for bit; estimates to 1e-12 relative)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1411_4942_gb300 import batch as B  # noqa: E402
+from paper_1411_4942_gb300 import pathsample as ps  # noqa: E402
+from paper_1411_4942_gb300 import serve as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def graph_set():
+    rs = np.random.default_rng(5)
+    graphs = []
+    for i in range(10):
+        scale = int(rs.integers(8, 13))
+        g = gg.rmat(scale, float(rs.integers(8, 33)), seed=300 + i)
+        # alternate adjacency variants: a batch may mix them
+        t = ps.make_tuning(adjacency=(ps.ADJ_HASH, ps.ADJ_SEARCH, ps.ADJ_VTAB)[i % 3])
+        graphs.append(ps.Graph(g.off, g.col, tuning=t))
+    return B.GraphSet(graphs)
+
+
+def _plain(gset, reqs):
+    h = B.run_plain(gset, reqs)
+    torch.cuda.synchronize()
+    return h.cpu().numpy().reshape(-1, 6).astype(np.uint64)
+
+
+def test_batched_equals_plain(graph_set):
+    rs = np.random.default_rng(7)
+    reqs = B.random_requests(rs, len(graph_set), log2_k=(10, 17))
+    want = _plain(graph_set, reqs)
+    for cfg in (B.LaunchConfig(256, 1 << 16, 0), B.LaunchConfig(128, 777, 3),
+                B.LaunchConfig(512, 1 << 12, 1)):
+        run = B.BatchRunner(graph_set, [B.Request(**vars(r)) for r in reqs], cfg)
+        run.launch()
+        torch.cuda.synchronize()
+        assert np.array_equal(run.histograms(), want)
+
+
+def test_cuda_graph_replay(graph_set):
+    rs = np.random.default_rng(8)
+    reqs = B.random_requests(rs, len(graph_set), log2_k=(12, 15))
+    want = _plain(graph_set, reqs)
+    run = B.BatchRunner(graph_set, reqs, B.LaunchConfig(256, 1 << 13))
+    run.capture()
+    for _ in range(2):
+        run.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(run.histograms(), want)
+
+
+def test_autotuner_choice_keeps_results(graph_set):
+    rs = np.random.default_rng(9)
+    reqs = B.random_requests(rs, len(graph_set), log2_k=(12, 15))
+    tuner = B.Autotuner(block_sizes=(128, 256), chunks=(1 << 12, 1 << 15), blocks_per_sm=(0,))
+    cfg = tuner.tune_launch(graph_set, reqs, budget_samples=1 << 18)
+    assert cfg in tuner.candidates and len(tuner.log) == len(tuner.candidates)
+    run = B.BatchRunner(graph_set, reqs, cfg)
+    run.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(run.histograms(), _plain(graph_set, reqs))
+    g = gg.rmat(11, 16.0, seed=3)
+    t = tuner.tune_graph_variant(g.off, g.col, k=1 << 16)
+    assert int(t.adjacency) in (ps.ADJ_HASH, ps.ADJ_SEARCH, ps.ADJ_VTAB)
+
+
+def _sources(n_graphs):
+    rs = np.random.default_rng(11)
+    out = {}
+    for i in range(n_graphs):
+        n = int(10 ** rs.uniform(3, 4))
+        gamma = float(rs.uniform(2.1, 2.8))
+        g = gg.chung_lu(n, 12.0, gamma, (12.0 * n) ** 0.5, 50 + i)
+        out[f"g{i}"] = (g.off, g.col)
+    return out
+
+
+@pytest.mark.parametrize("realtime", [True, False])
+def test_served_results_equal_requests_alone(realtime):
+    sources = _sources(6)
+    sizes = [ps.ps_graph_workspace_bytes(len(o) - 1, len(c)) for o, c in sources.values()]
+    budget = int(sum(sizes) * 0.6)  # forces evictions between requests
+    pool = S.GraphPool(sources, budget)
+    server = S.Server(pool, quantum=1 << 13, max_active=64, cfg=B.LaunchConfig(256, 1 << 12))
+    rs = np.random.default_rng(12)
+    reqs = S.poisson_requests(rs, list(sources), 120, 4000.0, log2_k=(8, 15))
+    results, report = server.run(reqs, realtime=realtime)
+    assert report["requests"] == len(reqs) == len(results)
+    assert report["graph_evictions"] > 0 and pool.used_bytes <= budget
+    assert report["latency_p99_ms"] >= report["latency_p50_ms"] > 0
+    alone, _ = S.run_sequential(S.GraphPool(sources, 10 * budget), reqs)
+    by_id = {rid: (h6, h4, est) for rid, h6, h4, est in alone}
+    for r in results:
+        h6, h4, est = by_id[r.rid]
+        assert r.hist6.tolist() == h6.tolist() and r.hist4.tolist() == h4.tolist()
+        np.testing.assert_allclose(r.est, est, rtol=1e-12)
