@@ -198,9 +198,12 @@ typedef struct {
  * n_graphs handles (each after ps_tau_prefix); d_items: device array of
  * n_items ps_work; d_hist: device uint64 [6 * slots] (added to); d_table:
  * device scratch of ps_batch_table_bytes(n_graphs) bytes (graph descriptors,
- * written by this call); d_counter: device uint32 scratch (zeroed by this
- * call).  Each item's counts equal those of the corresponding plain call.
- * Asynchronous. */
+ * written by this call); d_counter: device uint32 [2] (zeroed by this call;
+ * afterwards [1] holds the number of items skipped because their graph's
+ * adjacency variant differs from the one recorded for the table -- always 0
+ * for tables written by ps_batch_prepare).  Each item's counts equal those of
+ * the corresponding plain call.  When all graphs share one adjacency variant
+ * the launch uses a kernel specialised for it.  Asynchronous. */
 size_t ps_batch_table_bytes(int32_t n_graphs);
 int ps_batch_sample(const ps_graph *const *graphs, int32_t n_graphs, const ps_work *d_items,
                     int64_t n_items, uint64_t *d_hist, void *d_table, uint32_t *d_counter,

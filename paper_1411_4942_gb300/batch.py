@@ -63,8 +63,19 @@ class GraphSet:
         return sum(int(g.workspace.numel()) for g in self.graphs)
 
 
+def order_by_graph(items: np.ndarray) -> np.ndarray:
+    """Items grouped by graph, graphs with the most work first.  Resident
+    blocks take items in this order, so at any moment they share one graph's
+    working set (which then stays in L2) and the small graphs form the tail."""
+    if items.size == 0:
+        return items
+    g = items["graph"].astype(np.int64)
+    work = np.bincount(g, weights=items["count"].astype(np.float64))
+    return items[np.lexsort((items["first_id"], items["sampler"], g, -work[g]))]
+
+
 def plan_items(requests, chunk: int) -> tuple[np.ndarray, int]:
-    """Work items for the requests (largest first), and the number of slots."""
+    """Work items for the requests (grouped by graph), and the number of slots."""
     slots = 0
     for r in requests:
         if r.slot < 0:
@@ -78,9 +89,7 @@ def plan_items(requests, chunk: int) -> tuple[np.ndarray, int]:
             recs.append((r.first_id + done, r.seed, c, r.graph, r.slot, r.sampler))
             done += c
     items = np.array(recs, dtype=ps.WORK_DTYPE) if recs else np.zeros(0, dtype=ps.WORK_DTYPE)
-    if items.size:
-        items = items[np.argsort(-items["count"].astype(np.int64), kind="stable")]
-    return items, slots
+    return order_by_graph(items), slots
 
 
 class BatchRunner:
@@ -95,7 +104,7 @@ class BatchRunner:
         dev = gset.device
         self.d_items = torch.from_numpy(items.view(np.uint8).copy()).to(dev)
         self.d_hist = torch.zeros(6 * max(self.slots, 1), dtype=torch.int64, device=dev)
-        self.d_counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.d_counter = torch.zeros(2, dtype=torch.int32, device=dev)
         self.tuning = cfg.tuning()
         self.graph = None
 

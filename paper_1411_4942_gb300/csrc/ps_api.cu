@@ -435,14 +435,17 @@ size_t ps_batch_table_bytes(int32_t n_graphs) {
 int ps_batch_prepare(const ps_graph *const *graphs, int32_t n_graphs, void *d_table, ps_stream_t stream) {
     if (!graphs || n_graphs <= 0 || !d_table) return PS_ERR_ARG;
     std::vector<GraphDev> host(static_cast<size_t>(n_graphs));
+    int adj = graphs[0] ? graphs[0]->dev.adj_mode : 0;
     for (int32_t i = 0; i < n_graphs; i++) {
         if (!graphs[i]) return PS_ERR_ARG;
         if (!graphs[i]->prefixed) return PS_ERR_STATE;
         host[static_cast<size_t>(i)] = graphs[i]->dev;
+        if (graphs[i]->dev.adj_mode != adj) adj = 0;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     PS_CUDA_TRY(cudaMemcpyAsync(d_table, host.data(), host.size() * sizeof(GraphDev), cudaMemcpyHostToDevice, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));
+    note_table_adjacency(d_table, adj);
     return PS_OK;
 }
 

@@ -106,5 +106,7 @@ int launch_sampler(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, ui
                    uint64_t *d_hist, cudaStream_t s);
 int launch_batch(const void *d_table, int32_t n_graphs, const ps_work *d_items, int64_t n_items,
                  uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s);
+// Records the adjacency variant shared by a descriptor table's graphs (0: mixed).
+void note_table_adjacency(const void *d_table, int adj);
 
 }  // namespace ps

@@ -3,9 +3,11 @@
 Requests (graph, k, seed) arrive over time.  The server keeps graphs loaded
 (CSR, edge table, prefixes, adjacency structure) inside a device-memory
 budget, admits a request once its graph is resident and two histogram slots
-are free, and runs iterations: each iteration gives every admitted request
-with work left up to `quantum` more sample ids of each sampler and launches
-them all in one batched kernel.  Iterations alternate between streams, so a
+are free, and runs iterations: each iteration hands out up to
+`iteration_samples` sample ids per sampler, oldest admitted request first (at
+most `quantum` to one request), groups the work items by graph so the
+resident blocks share a graph's working set, and launches them all in one
+batched kernel.  Iterations alternate between streams, so a
 request that arrives while earlier work is on the GPU joins the next
 iteration and its kernel runs alongside.  A request finishes when the last
 iteration holding its samples finishes; its histograms are then read back
@@ -21,7 +23,7 @@ import time
 import numpy as np
 
 from . import pathsample as ps
-from .batch import LaunchConfig, SAMPLER_3PATH, SAMPLER_CENTRED
+from .batch import LaunchConfig, SAMPLER_3PATH, SAMPLER_CENTRED, order_by_graph
 
 
 @dataclasses.dataclass
@@ -140,18 +142,21 @@ class _Active:
 
 
 class Server:
-    def __init__(self, pool: GraphPool, quantum: int = 1 << 18, max_active: int = 1024,
-                 streams: int = 2, cfg: LaunchConfig | None = None, delta: float = 0.01):
+    def __init__(self, pool: GraphPool, quantum: int = 1 << 22, max_active: int = 1024,
+                 streams: int = 2, cfg: LaunchConfig | None = None, delta: float = 0.01,
+                 iteration_samples: int = 1 << 25):
         import torch
         self.pool = pool
         self.quantum = int(quantum)
+        # per-iteration cap (sample ids per sampler), filled oldest request first
+        self.iteration_samples = int(iteration_samples)
         self.max_active = int(max_active)
         self.cfg = cfg or LaunchConfig(block_size=256, chunk=1 << 16)
         self.delta = delta
         dev = pool.device
         self.streams = [torch.cuda.Stream(dev) for _ in range(streams)]
         self.d_hist = torch.zeros(12 * self.max_active, dtype=torch.int64, device=dev)
-        self.counters = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in self.streams]
+        self.counters = [torch.zeros(2, dtype=torch.int32, device=dev) for _ in self.streams]
         self.free_slots = list(range(self.max_active))[::-1]
         self.tuning = self.cfg.tuning()
         self.iterations = 0
@@ -243,8 +248,12 @@ class Server:
                 self.pool.sync_table()
                 recs = []
                 rids = []
-                for a in work:
-                    n_new = min(self.quantum, a.req.k - a.issued)
+                budget = self.iteration_samples
+                for a in work:  # admission order: the oldest requests first
+                    if budget <= 0:
+                        break
+                    n_new = min(self.quantum, a.req.k - a.issued, budget)
+                    budget -= n_new
                     for sampler in (SAMPLER_3PATH, SAMPLER_CENTRED):
                         done_ = 0
                         while done_ < n_new:
@@ -256,8 +265,7 @@ class Server:
                     a.outstanding += 1
                     total_samples += 2 * n_new
                     rids.append(a.req.rid)
-                items = np.array(recs, dtype=ps.WORK_DTYPE)
-                items = items[np.argsort(-items["count"].astype(np.int64), kind="stable")]
+                items = order_by_graph(np.array(recs, dtype=ps.WORK_DTYPE))
                 ev, keep = self._launch(turn % len(self.streams), items)
                 turn += 1
                 inflight.append((ev, rids, keep))

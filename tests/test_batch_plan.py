@@ -19,8 +19,12 @@ def test_items_cover_every_request_exactly_once():
             assert np.all(sel["seed"] == r.seed)
             ids = np.concatenate([np.arange(f, f + c) for f, c in zip(sel["first_id"], sel["count"])])
             assert np.array_equal(np.sort(ids), np.arange(r.first_id, r.first_id + r.k))
-        # largest items first (load balance of the persistent launch)
-        assert np.all(np.diff(items["count"].astype(np.int64)) <= 0)
+        # grouped by graph (each graph's items contiguous), most work first
+        g = items["graph"].astype(np.int64)
+        starts = np.flatnonzero(np.r_[True, g[1:] != g[:-1]])
+        assert len(starts) == len(set(g.tolist()))
+        work = [int(items["count"][g == gg_].sum()) for gg_ in g[starts]]
+        assert work == sorted(work, reverse=True)
 
 
 def test_slots_assigned_when_missing():

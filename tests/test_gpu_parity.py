@@ -264,7 +264,7 @@ def test_batched_launch_matches_plain_calls():
     d_items = torch.from_numpy(arr.view(np.uint8)).cuda()
     d_hist = torch.zeros(6 * slot, dtype=torch.int64, device="cuda")
     table = torch.empty(ps.ps_batch_table_bytes(len(Gs)), dtype=torch.uint8, device="cuda")
-    counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+    counter = torch.zeros(2, dtype=torch.int32, device="cuda")
     rc = ps.ps_batch_sample([G.handle for G in Gs], d_items.data_ptr(), len(items), d_hist.data_ptr(),
                             table.data_ptr(), counter.data_ptr())
     assert rc == ps.PS_OK
