@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "3-path samples/s (plain vs batched/served) at bit-exact histograms; HBM roofline %"
 UNIT = "samples/s"
 SECTOR = 32
-# Algorithmic bytes per sample (the paper's O(1) cost model of Theorem 3.4,
+# Algorithmic bytes per sample (the paper's O(1) cost model of Theorem 3.5,
 # one 32-byte sector per random access): 3-path = edge draw, edge record,
 # both endpoint offsets, the two neighbour reads and three adjacency lookups
 BYTES_3PATH = 9 * SECTOR

@@ -150,6 +150,14 @@ const char *ps_strerror(int code);
  * (all devices and threads).  For launch accounting in benchmarks. */
 uint64_t ps_kernel_launches(void);
 
+/* Self-test of failure detection: runs the bounded device wait that the
+ * library's single-pass scans use, on a flag that nothing ever sets, and
+ * returns the status the scans would report -- PS_ERR_TIMEOUT after
+ * spin_limit polls (32-256 ns each; capped at the library's own limit)
+ * instead of a hang.  d_scratch: device, 16 bytes, 16-byte aligned (cleared
+ * by the call).  Synchronises `stream`; the context stays usable. */
+int ps_selftest_bounded_wait(void *d_scratch, uint32_t spin_limit, ps_stream_t stream);
+
 /* Which array ps_graph_copy copies out. */
 #define PS_ARRAY_OFFSETS 0 /* int64 [n + 1]   canonical row offsets                      */
 #define PS_ARRAY_COLUMNS 1 /* int32 [nnz]     canonical sorted adjacency                 */

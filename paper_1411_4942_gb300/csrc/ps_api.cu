@@ -182,11 +182,31 @@ static void binomial_bar(uint64_t count, uint64_t k, double delta, double *pl, d
     *pu = 0.5 * (a + b);
 }
 
+// Runs the bounded wait of the scans on a flag that nothing sets.
+__global__ void k_wait_selftest(const uint32_t *flag, uint32_t limit, u64 *status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && wait_flag(flag, limit) == 0u) raise_flag(status, F_TIMEOUT);
+}
+
 }  // namespace ps
 
 using namespace ps;
 
 extern "C" {
+
+int ps_selftest_bounded_wait(void *d_scratch, uint32_t spin_limit, ps_stream_t stream) {
+    if (!d_scratch || (reinterpret_cast<uintptr_t>(d_scratch) & 15u) != 0) return PS_ERR_ARG;
+    if (spin_limit > kSpinLimit) spin_limit = kSpinLimit;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t *flag = static_cast<uint32_t *>(d_scratch);
+    u64 *status = reinterpret_cast<u64 *>(static_cast<char *>(d_scratch) + 8);
+    PS_CUDA_TRY(cudaMemsetAsync(d_scratch, 0, 16, s));
+    k_wait_selftest<<<1, 32, 0, s>>>(flag, spin_limit, status - ST_FLAGS);
+    PS_LAUNCH_CHECK();
+    uint64_t flags = 0;
+    PS_CUDA_TRY(cudaMemcpyAsync(&flags, status, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    PS_CUDA_TRY(cudaStreamSynchronize(s));
+    return flags_to_status(flags);
+}
 
 size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t) {
     Layout L;

@@ -75,6 +75,19 @@ __device__ __forceinline__ void raise_flag(u64 *status, u64 f) {
 // Bound on every device spin-wait (iterations with nanosleep back-off).
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p);
+
+// Waits until *flag is non-zero and returns it, or returns 0 after `limit`
+// polls (the caller then reports PS_ERR_TIMEOUT instead of hanging).
+__device__ __forceinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t limit) {
+    uint32_t f = ld_acquire(flag);
+    for (uint32_t it = 0; f == 0u && it < limit; it++) {
+        __nanosleep(it < 64 ? 32 : 256);
+        f = ld_acquire(flag);
+    }
+    return f;
+}
+
 // ------------------------------------------------------------------ loads
 
 __device__ __forceinline__ int32_t ldg_i32(const int32_t *p) { return __ldg(p); }
@@ -239,7 +252,7 @@ __device__ __forceinline__ bool adjacent_known(const GraphDev &g, int32_t a, int
 
 // ----------------------------------------------------------- edge hash set
 
-// The hash-table adjacency that the O(1) test of Theorem 3.4 assumes: the
+// The hash-table adjacency that the O(1) test of Theorem 3.5 assumes: the
 // edges {a, b}, a < b, keyed (a << 32) | b, in buckets of four 8-byte slots
 // (32 bytes, one DRAM sector) with linear probing from bucket to bucket.
 // Slots only ever go from empty (all ones) to full, so a lookup that meets a
@@ -323,7 +336,7 @@ __device__ __forceinline__ void eset_contains3(const uint64_t *set, uint64_t mas
 
 // ------------------------------------------------ per-vertex hash tables
 
-// Each adjacency list in its own open-addressing table (Theorem 3.4 assumes
+// Each adjacency list in its own open-addressing table (Theorem 3.5 assumes
 // hash-table adjacency lists): the table of vertex x is the 2 d_x int32
 // slots starting at 2 off(x), holding the neighbours of x (empty = -1),
 // linear probing with wrap-around inside the table.  The slot of y is
@@ -511,13 +524,7 @@ k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store
                 uint32_t f = 2u;
                 T val = identity;
                 if (p >= 0) {
-                    uint32_t it = 0;
-                    f = ld_acquire(st.flag + p);
-                    while (f == 0u) {
-                        if (++it >= kSpinLimit) break;
-                        __nanosleep(it < 64 ? 32 : 256);
-                        f = ld_acquire(st.flag + p);
-                    }
+                    f = wait_flag(st.flag + p, kSpinLimit);
                     if (f == 0u) {
                         timed_out = true;
                         f = 2u;

@@ -112,6 +112,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_batch_sample_prepared": ([V, I32, V, I64, V, V, V, V], I32),
             "ps_kernel_launches": ([], U64),
             "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
+            "ps_selftest_bounded_wait": ([V, ctypes.c_uint32, V], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -213,6 +214,11 @@ def ps_count_motifs_host(off: np.ndarray, col: np.ndarray, k3: int, kc: int, see
 
 def ps_kernel_launches() -> int:
     return int(load_library().ps_kernel_launches())
+
+
+def ps_selftest_bounded_wait(d_scratch: int, spin_limit: int, stream=None) -> int:
+    """The scans' bounded device wait on a flag nothing sets: PS_ERR_TIMEOUT."""
+    return int(load_library().ps_selftest_bounded_wait(d_scratch, spin_limit, _stream_ptr(stream)))
 
 
 PS_ERR_TOO_LARGE = -10

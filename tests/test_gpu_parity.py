@@ -149,6 +149,17 @@ def test_workspace_and_state_errors():
     ps.ps_graph_free(h)
 
 
+def test_bounded_wait_reports_timeout_and_context_survives():
+    # the scans' wait on a flag that nothing sets: a status, not a hang or trap
+    scratch = torch.zeros(4, dtype=torch.int32, device="cuda")
+    assert ps.ps_selftest_bounded_wait(scratch.data_ptr(), 2000) == ps.PS_ERR_TIMEOUT
+    assert ps.ps_selftest_bounded_wait(scratch.data_ptr() + 4, 10) == ps.PS_ERR_ARG
+    g = gg.gnp(50, 0.3, 2)
+    og, G = _check_structure(g)
+    h6, h4 = _hists(G, 10000, 10000, 1)
+    assert h6.tolist() == O.sample_3paths(og, 10000, 1).tolist()
+
+
 def test_degenerate_graphs():
     # no vertices, no edges, stars (W = 0), a single edge, and a triangle:
     # K3's edge (0, 1) has one later neighbour on each side, so Lambda = 1,
