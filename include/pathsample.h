@@ -91,23 +91,32 @@ size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
  * vertex by its rank in the order "d_u < d_v, ties by smaller id" (so the
  * order becomes integer order), rebuilds the adjacency lists sorted
  * ascending, and builds the edge table (u < v, u ascending then v ascending)
- * with the positions of each edge in both endpoint lists.
+ * with the positions of each edge in both endpoint lists, the raw weights
+ * tau_e and lambda_e, and (default adjacency) the hash set of the edges.
  *
  * d_off / d_col belong to the caller and are only read during the call.
  * d_workspace (ws_bytes >= ps_graph_workspace_bytes(n, nnz, t), 256-byte
  * aligned) must stay allocated and untouched until ps_graph_free(*out).
- * Synchronises `stream` (to read the validation flags).  On error *out is
- * NULL and the status is PS_ERR_ARG / PS_ERR_NOT_SIMPLE / PS_ERR_ASYMMETRIC
- * (highest-priority first) or PS_ERR_WORKSPACE / PS_ERR_CUDA. */
+ * Synchronises `stream` (to read the validation flags).  The hash set build
+ * (default adjacency), which only sampling reads, runs on a library-owned
+ * stream and may still be running when the call returns: ps_tau_prefix
+ * orders it before everything it queues on its own stream, and
+ * ps_graph_free waits for it.  On error *out is NULL and the status is
+ * PS_ERR_ARG / PS_ERR_NOT_SIMPLE / PS_ERR_ASYMMETRIC (highest-priority
+ * first) or PS_ERR_WORKSPACE / PS_ERR_CUDA. */
 int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_col,
                 void *d_workspace, size_t ws_bytes, const ps_tuning *t, ps_stream_t stream,
                 ps_graph **out);
 
 /* Section 3 (tau_e, W) and Section 4 (lambda_e, Lambda), the edge
- * distributions of Alg. 1 and Alg. 3: computes both weights of every edge, their inclusive uint64 prefix
- * sums (exact, so the edge draw is exact), N_1 of Alg. 2, the guide tables
- * of the inverse-CDF search and the hub adjacency bitmap.  Synchronises
- * `stream` and fills *out.  Returns PS_NO_PATHS when W == 0 or Lambda == 0
+ * distributions of Alg. 1 and Alg. 3: turns both weights of every edge into
+ * their inclusive uint64 prefix sums (exact, so the edge draw is exact),
+ * computes N_1 of Alg. 2, the guide tables of the inverse-CDF search and the
+ * structures of the chosen adjacency variant.  Synchronises `stream` once to
+ * read the totals and fills *out; the guide tables and adjacency structures
+ * are then finished in `stream` order, so sampling on another stream must
+ * first wait for `stream`.  A second call returns the same totals without
+ * recomputing.  Returns PS_NO_PATHS when W == 0 or Lambda == 0
  * (sampling then leaves histograms untouched), PS_ERR_OVERFLOW when a sum
  * does not fit in 64 bits, PS_ERR_TIMEOUT when the scan's bounded wait
  * expired. */
@@ -140,7 +149,10 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
                 const uint64_t hist4[4], uint64_t kc, double delta, double est[6],
                 double lo[6], double hi[6]);
 
-/* Releases the host metadata of g (not the workspace, which the caller owns). */
+/* Releases the host metadata of g (not the workspace, which the caller owns),
+ * first waiting for library work that may still write into the workspace
+ * (the hash set build of ps_load_csr); work the caller queued on its own
+ * streams is the caller's to wait for. */
 void ps_graph_free(ps_graph *g);
 
 /* Short description of a status code (static string). */

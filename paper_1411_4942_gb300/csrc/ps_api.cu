@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -45,6 +46,22 @@ int sm_count_of_current_device() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
     return sms > 0 ? sms : 1;
+}
+
+int get_side_streams(int device, cudaStream_t out[2]) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static cudaStream_t streams[kMaxDevices][2] = {};
+    if (device < 0 || device >= kMaxDevices) return PS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < 2; ++i)
+        if (!streams[device][i] && cudaStreamCreateWithFlags(&streams[device][i], cudaStreamNonBlocking) != cudaSuccess) {
+            streams[device][i] = nullptr;
+            return PS_ERR_CUDA;
+        }
+    out[0] = streams[device][0];
+    out[1] = streams[device][1];
+    return PS_OK;
 }
 
 int flags_to_status(uint64_t f) {
@@ -234,6 +251,12 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
         return PS_ERR_CUDA;
     }
     g->sm_count = sm_count_of_current_device();
+    for (cudaEvent_t &e : g->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            delete g;
+            return PS_ERR_CUDA;
+        }
     g->n = n;
     g->nnz = nnz;
     char *ws = g->ws;
@@ -263,6 +286,10 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
 
 int ps_tau_prefix(ps_graph *g, ps_stream_t stream, ps_stats *out) {
     if (!g) return PS_ERR_ARG;
+    if (g->prefixed) {  // already done: the prefixes are in place
+        if (out) *out = g->stats;
+        return (g->stats.W == 0 || g->stats.Lambda == 0) ? PS_NO_PATHS : PS_OK;
+    }
     DeviceGuard dg(g->device);
     if (!dg.ok) return PS_ERR_CUDA;
     const int rc = prefix_graph(g, reinterpret_cast<cudaStream_t>(stream));

@@ -90,19 +90,105 @@ __device__ __forceinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t lim
 
 // ------------------------------------------------------------------ loads
 
-__device__ __forceinline__ int32_t ldg_i32(const int32_t *p) { return __ldg(p); }
+// Read-only gathers of data written by earlier kernels.  PS_LOAD_MODE picks
+// the cache path: 0 = the non-coherent path through L1 (__ldg); 1 = L2 only
+// (ld.global.cg); 2 = non-coherent without L1 allocation.  In modes 1 and 2
+// a 32-byte edge record is one 256-bit load.
+#ifndef PS_LOAD_MODE
+#define PS_LOAD_MODE 0
+#endif
+#if PS_LOAD_MODE == 1
+#define PS_LD "ld.global.cg"
+#elif PS_LOAD_MODE == 2
+#define PS_LD "ld.global.nc.L1::no_allocate"
+#endif
+
+// L2 eviction priorities for the samplers' gathers (PS_L2_HINTS): 1 = the
+// uniformly random hash-bucket reads are evicted first, so they do not push
+// out the skewed hot data; 2 = also keep edge records, guide entries and
+// prefix probes (drawn in proportion to tau / lambda) with evict-last.
+#ifndef PS_L2_HINTS
+#define PS_L2_HINTS 0
+#endif
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ int32_t ldg_i32(const int32_t *p) {
+#if PS_LOAD_MODE == 0
+    return __ldg(p);
+#else
+    int32_t v;
+    asm(PS_LD ".s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#endif
+}
 __device__ __forceinline__ int64_t ldg_i64(const int64_t *p) {
+#if PS_LOAD_MODE == 0
     return static_cast<int64_t>(__ldg(reinterpret_cast<const long long *>(p)));
+#else
+    int64_t v;
+    asm(PS_LD ".s64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+#endif
 }
 __device__ __forceinline__ uint64_t ldg_u64(const uint64_t *p) {
+#if PS_LOAD_MODE == 0
     return static_cast<uint64_t>(__ldg(reinterpret_cast<const unsigned long long *>(p)));
+#else
+    uint64_t v;
+    asm(PS_LD ".u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+#endif
 }
+// Gathers of the skewed "hot" structures (guide entries, prefix probes).
+__device__ __forceinline__ int32_t ldg_i32_hot(const int32_t *p) {
+#if PS_L2_HINTS >= 2
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_policy_evict_last()));
+    return v;
+#else
+    return ldg_i32(p);
+#endif
+}
+__device__ __forceinline__ uint64_t ldg_u64_hot(const uint64_t *p) {
+#if PS_L2_HINTS >= 2
+    uint64_t v;
+    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(l2_policy_evict_last()));
+    return v;
+#else
+    return ldg_u64(p);
+#endif
+}
+
 __device__ __forceinline__ EdgeRec ldg_rec(const EdgeRec *p) {
-    const int4 *q = reinterpret_cast<const int4 *>(p);
-    int4 a = __ldg(q), b = __ldg(q + 1);
     EdgeRec e;
+#if PS_L2_HINTS >= 2
+    int4 a, b;
+    const uint64_t pol = l2_policy_evict_last();
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w) : "l"(reinterpret_cast<const int4 *>(p) + 1), "l"(pol));
     e.u = a.x; e.v = a.y; e.du = a.z; e.dv = a.w;
     e.iu = b.x; e.jv = b.y; e.ou = b.z; e.ov = b.w;
+#elif PS_LOAD_MODE == 0
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+    int4 a = __ldg(q), b = __ldg(q + 1);
+    e.u = a.x; e.v = a.y; e.du = a.z; e.dv = a.w;
+    e.iu = b.x; e.jv = b.y; e.ou = b.z; e.ov = b.w;
+#else
+    asm(PS_LD ".v8.s32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(e.u), "=r"(e.v), "=r"(e.du), "=r"(e.dv), "=r"(e.iu), "=r"(e.jv), "=r"(e.ou), "=r"(e.ov)
+        : "l"(p));
+#endif
     return e;
 }
 
@@ -193,7 +279,7 @@ __device__ __forceinline__ int64_t upper_bound_in(const uint64_t *P, int64_t lo,
                                                   uint64_t r) {
     while (lo < hi) {
         const int64_t mid = lo + ((hi - lo) >> 1);
-        if (ldg_u64(P + mid) > r) hi = mid;
+        if (ldg_u64_hot(P + mid) > r) hi = mid;
         else lo = mid + 1;
     }
     return lo;
@@ -204,8 +290,8 @@ __device__ __forceinline__ int64_t upper_bound_in(const uint64_t *P, int64_t lo,
 __device__ __forceinline__ int64_t find_edge(const uint64_t *P, const int32_t *G, int shift,
                                              uint64_t r) {
     const uint64_t b = r >> shift;
-    const int64_t lo = ldg_i32(G + b);
-    const int64_t hi = ldg_i32(G + b + 1);
+    const int64_t lo = ldg_i32_hot(G + b);
+    const int64_t hi = ldg_i32_hot(G + b + 1);
     if (lo == hi) return lo;
     return upper_bound_in(P, lo, hi, r);
 }
@@ -264,21 +350,41 @@ __device__ __forceinline__ uint64_t edge_key(int32_t a, int32_t b) {
     return (static_cast<uint64_t>(static_cast<uint32_t>(a)) << 32) | static_cast<uint32_t>(b);
 }
 
-__device__ __forceinline__ uint64_t key_bucket(uint64_t key, uint64_t mask) {
+// Mixes the key; its low bits pick the home bucket and its top two bits the
+// slot an insertion tries first (any slot order is valid for the lookups,
+// which read the whole bucket).
+__device__ __forceinline__ uint64_t key_hash(uint64_t key) {
     uint64_t h = key * 0x9E3779B97F4A7C15ull;
     h ^= h >> 31;
     h *= 0xD6E8FEB86659FD93ull;
     h ^= h >> 29;
-    return h & mask;
+    return h;
 }
+
+__device__ __forceinline__ uint64_t key_bucket(uint64_t key, uint64_t mask) { return key_hash(key) & mask; }
 
 struct Bucket {
     ulonglong2 lo, hi;
 };
 
 __device__ __forceinline__ Bucket load_bucket(const uint64_t *set, uint64_t b) {
+#if PS_L2_HINTS >= 1
+    Bucket k;
+    const uint64_t pol = l2_policy_evict_first();
+    const uint64_t *q = set + (b << 2);
+    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;" : "=l"(k.lo.x), "=l"(k.lo.y) : "l"(q), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;" : "=l"(k.hi.x), "=l"(k.hi.y) : "l"(q + 2), "l"(pol));
+    return k;
+#elif PS_LOAD_MODE == 0
     const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(set + (b << 2));
     return Bucket{__ldg(p), __ldg(p + 1)};
+#else
+    Bucket k;
+    asm(PS_LD ".v4.u64 {%0,%1,%2,%3}, [%4];"
+        : "=l"(k.lo.x), "=l"(k.lo.y), "=l"(k.hi.x), "=l"(k.hi.y)
+        : "l"(set + (b << 2)));
+    return k;
+#endif
 }
 
 // 1: key present, 0: absent, -1: bucket full without the key (probe on)
@@ -461,6 +567,10 @@ __device__ __forceinline__ U64x2 ld_cg<U64x2>(const U64x2 *p) {
 }
 
 // Scans `count` items: item i = load(i); store(i, exclusive_i, inclusive_i).
+// A tile is BLOCK * ITEMS consecutive items; warp w owns the w-th run of
+// 32 * ITEMS of them and walks it in rows of 32 (lane-contiguous, so loads
+// and stores coalesce), scanning each row across the warp and carrying the
+// row total forward.
 template <typename T, int BLOCK, int ITEMS, typename Op, typename Load, typename Store>
 __global__ void __launch_bounds__(BLOCK)
 k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store) {
@@ -472,23 +582,28 @@ k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store
     if (threadIdx.x == 0) s_tile = atomicAdd(st.counter, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t base = tile * (int64_t)(BLOCK * ITEMS) + (int64_t)threadIdx.x * ITEMS;
+    const int64_t wbase = tile * (int64_t)(BLOCK * ITEMS) + (int64_t)warp * (32 * ITEMS) + lane;
 
     T v[ITEMS];
 #pragma unroll
-    for (int i = 0; i < ITEMS; i++) v[i] = (base + i < count) ? load(base + i) : identity;
-#pragma unroll
-    for (int i = 1; i < ITEMS; i++) v[i] = op(v[i - 1], v[i]);
-    const T tsum = v[ITEMS - 1];
-    T x = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T y = shfl_up_t(x, o);
-        if (lane >= o) x = op(y, x);
+    for (int i = 0; i < ITEMS; i++) {
+        const int64_t idx = wbase + 32 * i;
+        v[i] = idx < count ? load(idx) : identity;
     }
-    T lane_excl = shfl_up_t(x, 1);
-    if (lane == 0) lane_excl = identity;
-    if (lane == 31) s_warp[warp] = x;
+    T carry = identity;
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        T x = v[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = shfl_up_t(x, o);
+            if (lane >= o) x = op(y, x);
+        }
+        x = op(carry, x);
+        v[i] = x;  // inclusive prefix within the warp's run
+        carry = shfl_idx_t(x, 31);
+    }
+    if (lane == 31) s_warp[warp] = carry;
     __syncthreads();
     if (warp == 0) {
         T w = lane < NW ? s_warp[lane] : identity;
@@ -552,14 +667,14 @@ k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store
         if (lane == 0) s_excl = excl;
     }
     __syncthreads();
-    // v[i] now holds this thread's inclusive prefix up to item i
-    const T run = op(s_excl, op(warp_excl, lane_excl));
+    const T run = op(s_excl, warp_excl);
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        if (base + i < count) {
-            const T exc = (i == 0) ? run : op(run, v[i - 1]);
-            store(base + i, exc, op(run, v[i]));
-        }
+        T prev = shfl_up_t(v[i], 1);
+        const T row_before = (i == 0) ? identity : shfl_idx_t(v[i - 1], 31);
+        if (lane == 0) prev = row_before;
+        const int64_t idx = wbase + 32 * i;
+        if (idx < count) store(idx, op(run, prev), op(run, v[i]));
     }
 }
 

@@ -72,6 +72,17 @@ struct ps_graph {
     bool prefixed;
     ps_stats stats;
     ps::GraphDev dev;
+    // ev[0..2]: fork / join events of this graph's calls; ev[3]: end of the
+    // edge hash set build, which runs on past ps_load_csr (eset_pending)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    mutable bool eset_pending = false;
+    ~ps_graph() {
+        // the hash set build writes into the caller's workspace: let it end
+        // (returns at once when it has, or was never started)
+        if (ev[3]) cudaEventSynchronize(ev[3]);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 namespace ps {
@@ -84,6 +95,19 @@ namespace ps {
 
 int sm_count_of_current_device();
 int flags_to_status(uint64_t flags);
+// Two non-blocking streams of `device` for independent kernels within one
+// call (created on first use, kept for the process; calls join them with
+// their own events, so concurrent calls stay ordered correctly).
+int get_side_streams(int device, cudaStream_t out[2]);
+
+// Makes `s` wait for a hash set build still running from ps_load_csr; every
+// call that reads the set (or the status words it writes) comes after this.
+inline int wait_eset(const ps_graph *g, cudaStream_t s) {
+    if (!g->eset_pending) return PS_OK;
+    if (cudaStreamWaitEvent(s, g->ev[3], 0) != cudaSuccess) return PS_ERR_CUDA;
+    g->eset_pending = false;
+    return PS_OK;
+}
 
 // Every kernel launch is followed by this: counts the launch (reported by
 // ps_kernel_launches) and checks the launch error.

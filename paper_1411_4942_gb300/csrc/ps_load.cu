@@ -489,10 +489,34 @@ struct StoreUbase {
 
 // Edge j = (u, v), u < v, in row-major order: j = ubase[u] + (iu - lowcnt[u]).
 // Each lower arc (v -> u, at position jv of N(v)) finds v in the upper part
-// of N(u) -- the shorter list, since u precedes v -- and writes the whole
-// record of its edge.  A lower arc without its upper partner means an
-// asymmetric input.
+// of N(u) and writes the whole 32-byte record of its edge: a full sector, so
+// the scattered writes cost no partial-sector traffic.  The upper part of
+// N(u) holds only neighbours of degree >= d_u, so it has at most sqrt(2m)
+// entries (the searches from the other side, in lower parts, are about 2^3.7
+// times longer on skewed graphs); the search halves it down to a window of
+// kEdgeWindow entries and then reads the whole window with independent loads
+// (one memory round trip instead of four dependent ones).  A lower arc
+// without its upper partner means an asymmetric input.
 constexpr int kEdgeItems = 8;
+constexpr int kEdgeWindow = 16;
+// Slots of a bucket are tried from the key's own first slot on, which spreads
+// the first attempts over the four slots (fewer failed compare-and-swaps than
+// always starting at slot 0).
+__device__ __forceinline__ bool eset_insert(uint64_t *set, uint64_t mask, uint64_t key) {
+    const uint64_t h = key_hash(key);
+    const int first = static_cast<int>(h >> 62);
+    uint64_t b = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + (b << 2));
+        for (int q = 0; q < 4; q++) {
+            const unsigned long long old = atomicCAS(slot + ((first + q) & 3), kEmptySlot, key);
+            if (old == kEmptySlot || old == key) return true;
+        }
+        b = (b + 1) & mask;
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(256)
 k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
         const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, EdgeRec *rec,
@@ -508,46 +532,116 @@ k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t 
             else hi = mid - 1;
         }
         int64_t r = lo;
+        int64_t ro = ldg_i64(coff + r);
         int64_t rend = ldg_i64(coff + r + 1);
         for (int t = 0; t < kEdgeItems; t++) {
             const int64_t i = i0 + t;
             if (i >= nnz) break;
             while (rend <= i) {
                 r++;
+                ro = rend;
                 rend = ldg_i64(coff + r + 1);
             }
             const int32_t x = ldg_i32(ccol + i);
             if (x >= r) continue;  // upper arcs are written from the other side
-            const int64_t ro = ldg_i64(coff + r);
-            const int32_t p = static_cast<int32_t>(i - ro);
             const int64_t ox = ldg_i64(coff + x);
             const int32_t lx = ldg_i32(lowcnt + x);
             const int64_t dx = ldg_i64(coff + x + 1) - ox;
-            int64_t a = ox + lx, b = ox + dx;  // lower_bound of r in the upper part
-            while (a < b) {
-                const int64_t mid = (a + b) >> 1;
-                if (ldg_i32(ccol + mid) < r) a = mid + 1;
+            // r sits in the upper part [a, b) of N(x) when the input is symmetric
+            int64_t a = ox + lx, b = ox + dx;
+            while (b - a > kEdgeWindow) {
+                const int64_t mid = a + ((b - a) >> 1);
+                if (ldg_i32(ccol + mid) <= r) a = mid;
                 else b = mid;
             }
-            if (a >= ox + dx || ldg_i32(ccol + a) != (int32_t)r) {
+            int below = 0;
+            bool hit = false;
+#pragma unroll
+            for (int w = 0; w < kEdgeWindow; w++)
+                if (a + w < b) {
+                    const int32_t c = ldg_i32(ccol + a + w);
+                    below += c < r;
+                    hit |= c == r;
+                }
+            if (!hit) {
                 asym = true;
                 continue;
             }
-            const int32_t iu = static_cast<int32_t>(a - ox);
+            const int32_t iu = static_cast<int32_t>(a + below - ox);
             const int64_t j = ldg_i64(ubase + x) + (iu - lx);
             if (j < 0 || j >= m_cap) {
                 asym = true;
                 continue;
             }
+            const int32_t dr = static_cast<int32_t>(rend - ro);
+            const int32_t p = static_cast<int32_t>(i - ro);
             int4 *e = reinterpret_cast<int4 *>(rec + j);
-            e[0] = make_int4(x, (int32_t)r, (int32_t)dx, (int32_t)(rend - ro));
-            e[1] = make_int4(iu, p, (int32_t)ox, (int32_t)ro);
+            e[0] = make_int4(x, static_cast<int32_t>(r), static_cast<int32_t>(dx), dr);
+            e[1] = make_int4(iu, p, static_cast<int32_t>(ox), static_cast<int32_t>(ro));
         }
     }
     if (asym) raise_flag(status, F_ASYM);
 }
 
+// Inserts every edge (u < v) of the edge table into the hash set with
+// compare-and-swap; the set's contents are deterministic, its slot layout is
+// not.  (A separate pass: inside the edge-table kernel the dependent CAS
+// chains stall threads that are already waiting on their searches, and
+// reading the keys from the sorted rows instead of the table's coalesced
+// (u, v) pairs measured 2.7x slower.)
+__global__ void __launch_bounds__(256)
+k_eset_build(int64_t m, const EdgeRec *__restrict__ rec, uint64_t *set, uint64_t mask, u64 *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool failed = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int2 uv = __ldg(reinterpret_cast<const int2 *>(rec + j));
+        failed |= !eset_insert(set, mask, edge_key(uv.x, uv.y));
+    }
+    if (failed) raise_flag(status, F_OVERFLOW);
+}
+
 // ------------------------------------------------------------------- driver
+
+// Runs independent kernels of one call on the device's side streams: fork()
+// makes them wait for the caller's stream, join() makes the caller's stream
+// wait for them.  The destructor joins on every return path, so no side work
+// outlives a call that failed halfway.  Without side streams every kernel
+// runs on the caller's stream.
+class SideFork {
+  public:
+    SideFork(ps_graph *g, cudaStream_t s) : g_(g), s_(s) { side_[0] = side_[1] = s; }
+    ~SideFork() { join(); }
+    SideFork(const SideFork &) = delete;
+    SideFork &operator=(const SideFork &) = delete;
+
+    int fork(int count) {
+        cudaStream_t side[2];
+        if (get_side_streams(g_->device, side) != PS_OK) return PS_OK;
+        PS_CUDA_TRY(cudaEventRecord(g_->ev[0], s_));
+        for (int i = 0; i < count; i++) {
+            PS_CUDA_TRY(cudaStreamWaitEvent(side[i], g_->ev[0], 0));
+            side_[i] = side[i];
+            used_ = i + 1;
+        }
+        return PS_OK;
+    }
+    cudaStream_t side(int i) const { return side_[i]; }
+    int join() {
+        int rc = PS_OK;
+        for (int i = 0; i < used_; i++)
+            if (cudaEventRecord(g_->ev[1 + i], side_[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s_, g_->ev[1 + i], 0) != cudaSuccess)
+                rc = PS_ERR_CUDA;
+        used_ = 0;
+        return rc;
+    }
+
+  private:
+    ps_graph *g_;
+    cudaStream_t s_;
+    cudaStream_t side_[2];
+    int used_ = 0;
+};
 
 int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStream_t s) {
     const Layout &L = g->L;
@@ -603,38 +697,67 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     k_tiers<<<1, 32, 0, s>>>(n, g->dnew, g->status);
     PS_LAUNCH_CHECK();
 
-    // (3) relabel + sort every row, by tier
+    // (3) relabel + sort every row, by tier; the tiers touch disjoint rows, so
+    // the long-row tiers run on side streams next to the short-row ones
     RowIn R{d_off, d_col, inv, g->rank, g->off, g->col, g->lowcnt, n, g->status};
     if (n > 0) {
-        k_sort_tier_a<<<sms * 16, 256, 0, s>>>(R);
-        PS_LAUNCH_CHECK();
-        k_sort_tier_b<<<sms * 4, 256, 0, s>>>(R);
-        PS_LAUNCH_CHECK();
+        SideFork fork(g, s);
         if (g->d_max > kTierB) {
-            const int smem = kTierC * (int)sizeof(int32_t);
-            k_sort_tier_c<<<sms * 4, 512, smem, s>>>(R);
-            PS_LAUNCH_CHECK();
+            rc = fork.fork(2);
+            if (rc) return rc;
         }
         if (g->d_max > kTierC) {
             int vb = 0;
             while (vb < 31 && (static_cast<uint64_t>(n - 1) >> vb) != 0) vb++;
-            k_sort_tier_d<<<sms * 2, 1024, 0, s>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
+            k_sort_tier_d<<<sms * 2, 1024, 0, fork.side(1)>>>(R, reinterpret_cast<int32_t *>(g->rec), vb);
             PS_LAUNCH_CHECK();
         }
+        if (g->d_max > kTierB) {
+            const int smem = kTierC * (int)sizeof(int32_t);
+            k_sort_tier_c<<<sms * 4, 512, smem, fork.side(0)>>>(R);
+            PS_LAUNCH_CHECK();
+        }
+        k_sort_tier_b<<<sms * 4, 256, 0, s>>>(R);
+        PS_LAUNCH_CHECK();
+        k_sort_tier_a<<<sms * 16, 256, 0, s>>>(R);
+        PS_LAUNCH_CHECK();
+        rc = fork.join();
+        if (rc) return rc;
     }
 
-    // (4) edge numbering and the edge table
+    // (4) the edge numbering and the edge table
     PS_CUDA_TRY(cudaMemsetAsync(g->ubase, 0, sizeof(int64_t), s));
     rc = run_scan<int64_t>(g, 2, n, (int64_t)0, OpSum(), LoadUp{g->dnew, g->lowcnt},
                            StoreUbase{g->ubase, n, g->status}, s);
     if (rc) return rc;
     if (nnz > 0) {
-        int64_t chunks = (nnz + kEdgeItems - 1) / kEdgeItems;
-        int64_t blocks = (chunks + 255) / 256;
+        int64_t blocks = ((nnz + kEdgeItems - 1) / kEdgeItems + 255) / 256;
         if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
         k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->rec,
                                                  L.m_cap, g->status);
         PS_LAUNCH_CHECK();
+    }
+
+    // (5) the edge hash set.  Only sampling reads it, so it is built on a side
+    // stream and left running: the caller's stream goes on to the prefixes,
+    // which wait for it only before their final status read (wait_eset).
+    if (nnz > 0 && g->eset) {
+        cudaStream_t es = s;
+        cudaStream_t side[2];
+        if (get_side_streams(g->device, side) == PS_OK) {
+            PS_CUDA_TRY(cudaEventRecord(g->ev[0], s));
+            PS_CUDA_TRY(cudaStreamWaitEvent(side[0], g->ev[0], 0));
+            es = side[0];
+        }
+        g->eset_pending = true;
+        const uint64_t eset_mask = static_cast<uint64_t>(L.eset_buckets - 1);
+        PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * 4 * L.eset_buckets, es));
+        int64_t eb = (L.m_cap + 255) / 256;
+        if (eb > (int64_t)sms * 32) eb = (int64_t)sms * 32;
+        if (eb < 1) eb = 1;
+        k_eset_build<<<(unsigned)eb, 256, 0, es>>>(L.m_cap, g->rec, g->eset, eset_mask, g->status);
+        PS_LAUNCH_CHECK();
+        PS_CUDA_TRY(cudaEventRecord(g->ev[3], es));
     }
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -15,6 +15,8 @@ __device__ __forceinline__ U64x2 weights(const EdgeRec &e) {
     return U64x2{t, l};
 }
 
+// The scan reads the edge records in order (the edge-table kernel writes them
+// scattered, where the 8-byte weights would be partial-sector writes).
 struct LoadWeights {
     const EdgeRec *rec;
     __device__ U64x2 operator()(int64_t j) const { return weights(ldg_rec(rec + j)); }
@@ -145,33 +147,6 @@ k_hub_bits(int64_t hub_start, int64_t n, const int64_t *__restrict__ coff, const
     }
 }
 
-// Inserts every edge (u < v) into the hash set; slots are claimed with
-// compare-and-swap, so the set's contents (not its layout) are deterministic.
-__global__ void __launch_bounds__(256)
-k_eset_build(int64_t m, const EdgeRec *__restrict__ rec, uint64_t *set, uint64_t mask, u64 *status) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    bool failed = false;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const int2 uv = __ldg(reinterpret_cast<const int2 *>(rec + j));
-        const uint64_t key = edge_key(uv.x, uv.y);
-        uint64_t b = key_bucket(key, mask);
-        bool done = false;
-        for (uint64_t probe = 0; probe <= mask && !done; probe++) {
-            unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + (b << 2));
-            for (int s = 0; s < 4; s++) {
-                const unsigned long long old = atomicCAS(slot + s, kEmptySlot, key);
-                if (old == kEmptySlot || old == key) {
-                    done = true;
-                    break;
-                }
-            }
-            b = (b + 1) & mask;
-        }
-        failed |= !done;
-    }
-    if (failed) raise_flag(status, F_OVERFLOW);
-}
-
 // Inserts every arc (x -> y) into the table of x with compare-and-swap; the
 // tables' contents are deterministic, their slot layout is not.
 constexpr int kVtabItems = 8;
@@ -281,17 +256,8 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     S.tau_shift = tshift;
     S.lambda_shift = lshift;
 
-    // edge hash set
+    // the edge hash set is filled by the load step (on a side stream)
     const uint64_t eset_mask = g->L.eset_buckets > 0 ? static_cast<uint64_t>(g->L.eset_buckets - 1) : 0;
-    if (g->eset) {
-        PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * 4 * g->L.eset_buckets, s));
-        if (m > 0) {
-            int64_t blocks = (m + 255) / 256;
-            if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
-            k_eset_build<<<(unsigned)blocks, 256, 0, s>>>(m, g->rec, g->eset, eset_mask, g->status);
-            PS_LAUNCH_CHECK();
-        }
-    }
 
     // per-vertex hash tables
     if (g->vtab) {
@@ -315,9 +281,10 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         k_hub_bits<<<(unsigned)blocks, 256, 0, s>>>(n - hubs, n, g->off, g->col, g->hub, g->L.hub_words);
         PS_LAUNCH_CHECK();
     }
-    // The kernels queued after the synchronisation cannot fail on valid
-    // state (the hash set's load is at most 1/2, so every insertion finds a
-    // slot); later calls on `stream` are ordered after them.
+    // The kernels queued after the synchronisation, and the hash set build,
+    // cannot fail on valid state (the hash set's load is at most 1/2, so
+    // every insertion finds a slot); later calls on `stream` are ordered
+    // after them.
 
     GraphDev &D = g->dev;
     D.eset = g->eset;
@@ -341,6 +308,10 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     D.hub_words = static_cast<int32_t>(g->L.hub_words);
     D.tau_shift = tshift;
     D.lam_shift = lshift;
+    // the hash set build of the load step ran beside everything above; later
+    // calls on `s` come after it too
+    const int rc = wait_eset(g, s);
+    if (rc) return rc;
     g->prefixed = true;
     return (S.W == 0 || S.Lambda == 0) ? PS_NO_PATHS : PS_OK;
 }

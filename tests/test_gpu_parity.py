@@ -285,6 +285,28 @@ def test_batched_launch_matches_plain_calls():
         assert got[s].tolist() == h.cpu().numpy()[:6].tolist()
 
 
+def test_social_chung_lu_3m_full_size_parity():
+    """Social-network-shaped Chung-Lu: n = 3,000,000, exponent 2.1, max weight
+    33,000, mean weight 78 (~117M edges); W, Lambda, N_1 and both prefixes in
+    full, histograms at the full k = 2^27 (3-path) and 2^26 (centred)."""
+    g = gg.social_chung_lu_3m()
+    G = _load(g)
+    og = O.prepare(g.off, g.col)
+    st = G.stats
+    assert (int(st.W), int(st.Lambda), st.N1, int(st.m)) == (og.W, og.Lambda, og.N1, og.m)
+    assert np.array_equal(G.copy(ps.PS_ARRAY_PTAU), og.ptau)
+    assert np.array_equal(G.copy(ps.PS_ARRAY_PLAMBDA), og.plam)
+    rec = G.copy(ps.PS_ARRAY_EDGES)
+    assert np.array_equal(rec[:, 4], og.eiu) and np.array_equal(rec[:, 5], og.ejv)
+    del rec
+    h6 = G.sample_3paths(1 << 27, 3)
+    h4 = G.sample_centered(1 << 26, 3)
+    torch.cuda.synchronize()
+    threads = max(1, O.max_threads())
+    assert h6.cpu().numpy()[:6].tolist() == O.sample_3paths(og, 1 << 27, 3, threads=threads).tolist()
+    assert h4.cpu().numpy()[:4].tolist() == O.sample_centered(og, 1 << 26, 3, threads=threads).tolist()
+
+
 def test_rmat20_full_size_parity():
     """R-MAT scale 20, edge factor 16, (0.57, 0.19, 0.19, 0.05), seed 11:
     prefixes compared in full, histograms at the full k = 2^24 per sampler
