@@ -254,11 +254,89 @@ __device__ __forceinline__ int next_pow2(int d) {
     return p;
 }
 
-// Tier B: rows of 33..1024 entries, one warp, bitonic network in shared memory.
-__global__ void __launch_bounds__(256) k_sort_tier_b(RowIn R) {
-    __shared__ int32_t s_buf[8][kTierB];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *buf = s_buf[warp];
+// Bitonic sort, ascending, of N = E * THREADS keys held E per thread in
+// blocked order (thread t holds keys t*E .. t*E + E - 1).  A compare-exchange
+// stage whose partner key sits in the same thread works on registers, one
+// whose partner sits in the same warp exchanges by shuffle, and only the
+// stages that cross warps go through shared memory (smem: N keys; unused
+// when THREADS == 32).  Fully unrolled, so every register index is static.
+template <int E, int THREADS>
+__device__ __forceinline__ void bitonic_blocked(int32_t (&x)[E], int32_t *smem) {
+    constexpr int N = E * THREADS;
+    const int lane = threadIdx.x & 31;
+    const int base = (THREADS == 32 ? lane : static_cast<int>(threadIdx.x)) * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int i = 0; i < E; i++)
+                    if ((i & j) == 0) {
+                        const bool asc = ((base | i) & k) == 0;
+                        const int32_t a = x[i], b = x[i | j];
+                        x[i] = asc ? min(a, b) : max(a, b);
+                        x[i | j] = asc ? max(a, b) : min(a, b);
+                    }
+            } else if (j < 32 * E) {
+                const int lm = j / E;
+                const bool keep_min = ((lane & lm) == 0) == ((base & k) == 0);
+#pragma unroll
+                for (int i = 0; i < E; i++) {
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, x[i], lm);
+                    x[i] = keep_min ? min(x[i], y) : max(x[i], y);
+                }
+            } else if (THREADS > 32) {
+                __syncthreads();  // the previous stage's readers are done
+#pragma unroll
+                for (int i = 0; i < E; i++) smem[base + i] = x[i];
+                __syncthreads();
+                const bool keep_min = ((base & j) == 0) == ((base & k) == 0);
+#pragma unroll
+                for (int i = 0; i < E; i++) {
+                    const int32_t y = smem[(base + i) ^ j];
+                    x[i] = keep_min ? min(x[i], y) : max(x[i], y);
+                }
+            }
+        }
+    }
+}
+
+// One row of tier B with P = 32 * E slots: relabel, sort in registers, write
+// the row and its lower count.
+template <int E>
+__device__ __forceinline__ void sort_row_warp(const RowIn &R, int64_t r, uint32_t v, int64_t o, int d,
+                                              bool &bad, bool &nsimple) {
+    const int lane = threadIdx.x & 31;
+    int32_t x[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = lane * E + i;
+        x[i] = idx < d ? relabel(R, o + idx, v, static_cast<int32_t>(r), bad, nsimple) : INT_MAX;
+    }
+    bitonic_blocked<E, 32>(x, nullptr);
+    const int32_t after = __shfl_down_sync(0xffffffffu, x[0], 1);  // first key of the next lane
+    int32_t *dst = R.ccol + R.coff[r];
+    int low = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = lane * E + i;
+        if (idx < d) {
+            dst[idx] = x[i];
+            low += x[i] < static_cast<int32_t>(r);
+            const int32_t nx = (i + 1 < E) ? x[i + 1] : after;
+            if (idx + 1 < d && nx == x[i]) nsimple = true;
+        }
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+    if (lane == 0) R.lowcnt[r] = low;
+}
+
+// Tier B: rows of 33..1024 entries, one warp, bitonic network in registers.
+// (Capped at 64 registers: four blocks per SM beat the spill-free 105-register
+// build; the same holds for tier C at three blocks.)
+__global__ void __launch_bounds__(256, 4) k_sort_tier_b(RowIn R) {
     const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 1]);
     const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 2]);
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
@@ -267,43 +345,55 @@ __global__ void __launch_bounds__(256) k_sort_tier_b(RowIn R) {
         const uint32_t v = R.inv[r];
         const int64_t o = ldg_i64(R.off + v);
         const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
-        const int P = next_pow2(d);
-        for (int i = lane; i < P; i += 32)
-            buf[i] = (i < d) ? relabel(R, o + i, v, (int32_t)r, bad, nsimple) : INT_MAX;
-        __syncwarp();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = lane; i < (P >> 1); i += 32) {
-                    const int e = 2 * i - (i & (j - 1));
-                    const int32_t a = buf[e], b = buf[e + j];
-                    const bool asc = (e & k) == 0;
-                    if ((a > b) == asc) {
-                        buf[e] = b;
-                        buf[e + j] = a;
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        int low = 0;
-        int32_t *dst = R.ccol + R.coff[r];
-        for (int i = lane; i < d; i += 32) {
-            const int32_t x = buf[i];
-            dst[i] = x;
-            low += (x < (int32_t)r);
-            if (i + 1 < d && buf[i + 1] == x) nsimple = true;
-        }
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
-        if (lane == 0) R.lowcnt[r] = low;
-        __syncwarp();
+        if (d <= 64) sort_row_warp<2>(R, r, v, o, d, bad, nsimple);
+        else if (d <= 128) sort_row_warp<4>(R, r, v, o, d, bad, nsimple);
+        else if (d <= 256) sort_row_warp<8>(R, r, v, o, d, bad, nsimple);
+        else if (d <= 512) sort_row_warp<16>(R, r, v, o, d, bad, nsimple);
+        else sort_row_warp<32>(R, r, v, o, d, bad, nsimple);
     }
     report(R, bad, nsimple);
 }
 
-// Tier C: rows of 1025..4096 entries, one block of 512, shared-memory bitonic
-// (16 KB, several blocks per SM).
-__global__ void __launch_bounds__(512) k_sort_tier_c(RowIn R) {
+// Tier C: rows of 1025..4096 entries, one block of 512, bitonic network in
+// registers with the cross-warp stages in shared memory (16 KB, several
+// blocks per SM).
+template <int E>
+__device__ __forceinline__ void sort_row_block(const RowIn &R, int64_t r, uint32_t v, int64_t o, int d,
+                                               int32_t *smem, int *s_low, bool &bad, bool &nsimple) {
+    constexpr int kThreads = 512;
+    const int base = static_cast<int>(threadIdx.x) * E;
+    int32_t x[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = base + i;
+        x[i] = idx < d ? relabel(R, o + idx, v, static_cast<int32_t>(r), bad, nsimple) : INT_MAX;
+    }
+    if (threadIdx.x == 0) *s_low = 0;
+    bitonic_blocked<E, kThreads>(x, smem);
+    __syncthreads();  // the sort's last shared-memory readers are done
+#pragma unroll
+    for (int i = 0; i < E; i++) smem[base + i] = x[i];
+    __syncthreads();
+    int32_t *dst = R.ccol + R.coff[r];
+    int low = 0;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = base + i;
+        if (idx < d) {
+            dst[idx] = x[i];
+            low += x[i] < static_cast<int32_t>(r);
+            if (idx + 1 < d && smem[idx + 1] == x[i]) nsimple = true;
+        }
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+    if ((threadIdx.x & 31) == 0) atomicAdd(s_low, low);
+    __syncthreads();
+    if (threadIdx.x == 0) R.lowcnt[r] = *s_low;
+    __syncthreads();  // s_low and smem are free for the next row
+}
+
+__global__ void __launch_bounds__(512, 3) k_sort_tier_c(RowIn R) {
     extern __shared__ int32_t s_dyn[];
     __shared__ int s_low;
     const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 2]);
@@ -313,39 +403,8 @@ __global__ void __launch_bounds__(512) k_sort_tier_c(RowIn R) {
         const uint32_t v = R.inv[r];
         const int64_t o = ldg_i64(R.off + v);
         const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
-        const int P = next_pow2(d);
-        if (threadIdx.x == 0) s_low = 0;
-        for (int i = threadIdx.x; i < P; i += blockDim.x)
-            s_dyn[i] = (i < d) ? relabel(R, o + i, v, (int32_t)r, bad, nsimple) : INT_MAX;
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
-                    const int e = 2 * i - (i & (j - 1));
-                    const int32_t a = s_dyn[e], b = s_dyn[e + j];
-                    const bool asc = (e & k) == 0;
-                    if ((a > b) == asc) {
-                        s_dyn[e] = b;
-                        s_dyn[e + j] = a;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        int low = 0;
-        int32_t *dst = R.ccol + R.coff[r];
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            const int32_t x = s_dyn[i];
-            dst[i] = x;
-            low += (x < (int32_t)r);
-            if (i + 1 < d && s_dyn[i + 1] == x) nsimple = true;
-        }
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_low, low);
-        __syncthreads();
-        if (threadIdx.x == 0) R.lowcnt[r] = s_low;
-        __syncthreads();
+        if (d <= 2048) sort_row_block<4>(R, r, v, o, d, s_dyn, &s_low, bad, nsimple);
+        else sort_row_block<8>(R, r, v, o, d, s_dyn, &s_low, bad, nsimple);
     }
     report(R, bad, nsimple);
 }
