@@ -8,13 +8,14 @@
 
 #include "../../include/pathsample.h"
 #include "ps_device.cuh"
+#include "ps_scan.cuh"
 
 namespace ps {
 
 // Sort tiers of the row relabel-and-sort step, by row length.
-constexpr int kTierA = 32;      // one warp, registers
-constexpr int kTierB = 1024;    // one warp, shared memory
-constexpr int kTierC = 4096;    // one block, shared memory (16 KB); above: block radix sort
+constexpr int kTierA = 32;      // one warp, one key per lane
+constexpr int kTierB = 1024;    // one warp, up to 32 keys per lane in registers
+constexpr int kTierC = 4096;    // one block, registers + 16 KB shared; above: block radix sort
 // Hub rows are only worth a bitmap above this degree.
 constexpr int kHubMinDegree = 64;
 // Items per tile of every scan.
