@@ -110,12 +110,12 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     if (l.gcap < 2) l.gcap = 2;
     l.hub_cap = t.hub_count;
     l.hub_words = (n + 31) / 32;
-    // edge hash set: a power-of-two number of 4-slot buckets, load <= 1/2
+    // edge hash set: a power-of-two number of buckets, load <= 1/2
     l.eset_buckets = 0;
     if (t.adj_mode == kAdjHash) {
         int64_t slots = 64;
         while (slots < 2 * l.m_cap) slots <<= 1;
-        l.eset_buckets = slots / 4;
+        l.eset_buckets = slots / kBucketSlots;
     }
     l.vtab_slots = t.adj_mode == kAdjVtab ? 2 * nnz : 0;
     l.radix_tiles = (n + kRadixTile - 1) / kRadixTile;
@@ -146,7 +146,7 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.gtau = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
     l.glam = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
     l.hub = take(static_cast<size_t>(l.hub_cap) * l.hub_words * sizeof(uint32_t));
-    l.eset = take(static_cast<size_t>(l.eset_buckets) * 4 * sizeof(uint64_t));
+    l.eset = take(static_cast<size_t>(l.eset_buckets) * kBucketSlots * sizeof(uint64_t));
     l.vtab = take(static_cast<size_t>(l.vtab_slots) * sizeof(int32_t));
     l.keys0 = take(n1 * sizeof(uint32_t));
     l.keys1 = take(n1 * sizeof(uint32_t));

@@ -103,24 +103,6 @@ __device__ __forceinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t lim
 #define PS_LD "ld.global.nc.L1::no_allocate"
 #endif
 
-// L2 eviction priorities for the samplers' gathers (PS_L2_HINTS): 1 = the
-// uniformly random hash-bucket reads are evicted first, so they do not push
-// out the skewed hot data; 2 = also keep edge records, guide entries and
-// prefix probes (drawn in proportion to tau / lambda) with evict-last.
-#ifndef PS_L2_HINTS
-#define PS_L2_HINTS 0
-#endif
-__device__ __forceinline__ uint64_t l2_policy_evict_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
 __device__ __forceinline__ int32_t ldg_i32(const int32_t *p) {
 #if PS_LOAD_MODE == 0
     return __ldg(p);
@@ -149,37 +131,14 @@ __device__ __forceinline__ uint64_t ldg_u64(const uint64_t *p) {
 #endif
 }
 // Gathers of the skewed "hot" structures (guide entries, prefix probes).
-__device__ __forceinline__ int32_t ldg_i32_hot(const int32_t *p) {
-#if PS_L2_HINTS >= 2
-    int32_t v;
-    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_policy_evict_last()));
-    return v;
-#else
-    return ldg_i32(p);
-#endif
-}
-__device__ __forceinline__ uint64_t ldg_u64_hot(const uint64_t *p) {
-#if PS_L2_HINTS >= 2
-    uint64_t v;
-    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(l2_policy_evict_last()));
-    return v;
-#else
-    return ldg_u64(p);
-#endif
-}
+// (Evict-last L2 hints on these and evict-first on the hash buckets were
+// measured: no gain.)
+__device__ __forceinline__ int32_t ldg_i32_hot(const int32_t *p) { return ldg_i32(p); }
+__device__ __forceinline__ uint64_t ldg_u64_hot(const uint64_t *p) { return ldg_u64(p); }
 
 __device__ __forceinline__ EdgeRec ldg_rec(const EdgeRec *p) {
     EdgeRec e;
-#if PS_L2_HINTS >= 2
-    int4 a, b;
-    const uint64_t pol = l2_policy_evict_last();
-    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "l"(p), "l"(pol));
-    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w) : "l"(reinterpret_cast<const int4 *>(p) + 1), "l"(pol));
-    e.u = a.x; e.v = a.y; e.du = a.z; e.dv = a.w;
-    e.iu = b.x; e.jv = b.y; e.ou = b.z; e.ov = b.w;
-#elif PS_LOAD_MODE == 0
+#if PS_LOAD_MODE == 0
     const int4 *q = reinterpret_cast<const int4 *>(p);
     int4 a = __ldg(q), b = __ldg(q + 1);
     e.u = a.x; e.v = a.y; e.du = a.z; e.dv = a.w;
@@ -341,18 +300,23 @@ __device__ __forceinline__ bool adjacent_known(const GraphDev &g, int32_t a, int
 // The hash-table adjacency that the O(1) test of Theorem 3.5 assumes: the
 // edges {a, b}, a < b, keyed (a << 32) | b, in buckets of four 8-byte slots
 // (32 bytes, one DRAM sector) with linear probing from bucket to bucket.
+// (8-slot, 64-byte buckets overflow less -- 1.04 instead of 1.18 buckets per
+// absent-key lookup at load 1/2 -- but measured slower: 3-path sampling
+// 1.75 -> 1.88 ms on R-MAT 20 and 20 -> 29 ms on the 3M-vertex graph.)
 // Slots only ever go from empty (all ones) to full, so a lookup that meets a
 // bucket with an empty slot before finding its key can stop: had the key
 // been inserted, it would sit in that bucket or an earlier one.
 constexpr uint64_t kEmptySlot = ~0ull;
+constexpr int kBucketSlots = 4;
+constexpr int kBucketShift = 2;  // log2(kBucketSlots)
 
 __device__ __forceinline__ uint64_t edge_key(int32_t a, int32_t b) {
     return (static_cast<uint64_t>(static_cast<uint32_t>(a)) << 32) | static_cast<uint32_t>(b);
 }
 
-// Mixes the key; its low bits pick the home bucket and its top two bits the
-// slot an insertion tries first (any slot order is valid for the lookups,
-// which read the whole bucket).
+// Mixes the key; its low bits pick the home bucket and its top kBucketShift
+// bits the slot an insertion tries first (any slot order is valid for the
+// lookups, which read the whole bucket).
 __device__ __forceinline__ uint64_t key_hash(uint64_t key) {
     uint64_t h = key * 0x9E3779B97F4A7C15ull;
     h ^= h >> 31;
@@ -364,35 +328,26 @@ __device__ __forceinline__ uint64_t key_hash(uint64_t key) {
 __device__ __forceinline__ uint64_t key_bucket(uint64_t key, uint64_t mask) { return key_hash(key) & mask; }
 
 struct Bucket {
-    ulonglong2 lo, hi;
+    ulonglong2 q[kBucketSlots / 2];
 };
 
 __device__ __forceinline__ Bucket load_bucket(const uint64_t *set, uint64_t b) {
-#if PS_L2_HINTS >= 1
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(set + (b << kBucketShift));
     Bucket k;
-    const uint64_t pol = l2_policy_evict_first();
-    const uint64_t *q = set + (b << 2);
-    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;" : "=l"(k.lo.x), "=l"(k.lo.y) : "l"(q), "l"(pol));
-    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;" : "=l"(k.hi.x), "=l"(k.hi.y) : "l"(q + 2), "l"(pol));
+#pragma unroll
+    for (int i = 0; i < kBucketSlots / 2; i++) k.q[i] = __ldg(p + i);
     return k;
-#elif PS_LOAD_MODE == 0
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(set + (b << 2));
-    return Bucket{__ldg(p), __ldg(p + 1)};
-#else
-    Bucket k;
-    asm(PS_LD ".v4.u64 {%0,%1,%2,%3}, [%4];"
-        : "=l"(k.lo.x), "=l"(k.lo.y), "=l"(k.hi.x), "=l"(k.hi.y)
-        : "l"(set + (b << 2)));
-    return k;
-#endif
 }
 
 // 1: key present, 0: absent, -1: bucket full without the key (probe on)
 __device__ __forceinline__ int bucket_verdict(const Bucket &k, uint64_t key) {
-    if (k.lo.x == key || k.lo.y == key || k.hi.x == key || k.hi.y == key) return 1;
-    if (k.lo.x == kEmptySlot || k.lo.y == kEmptySlot || k.hi.x == kEmptySlot || k.hi.y == kEmptySlot)
-        return 0;
-    return -1;
+    bool hit = false, empty = false;
+#pragma unroll
+    for (int i = 0; i < kBucketSlots / 2; i++) {
+        hit |= (k.q[i].x == key) | (k.q[i].y == key);
+        empty |= (k.q[i].x == kEmptySlot) | (k.q[i].y == kEmptySlot);
+    }
+    return hit ? 1 : (empty ? 0 : -1);
 }
 
 static __device__ __noinline__ bool probe_on(const uint64_t *set, uint64_t mask, uint64_t key,

@@ -563,12 +563,13 @@ constexpr int kEdgeWindow = 16;
 // always starting at slot 0).
 __device__ __forceinline__ bool eset_insert(uint64_t *set, uint64_t mask, uint64_t key) {
     const uint64_t h = key_hash(key);
-    const int first = static_cast<int>(h >> 62);
+    const int first = static_cast<int>(h >> (64 - kBucketShift));
     uint64_t b = h & mask;
     for (uint64_t probe = 0; probe <= mask; probe++) {
-        unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + (b << 2));
-        for (int q = 0; q < 4; q++) {
-            const unsigned long long old = atomicCAS(slot + ((first + q) & 3), kEmptySlot, key);
+        unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + (b << kBucketShift));
+        for (int q = 0; q < kBucketSlots; q++) {
+            const unsigned long long old =
+                atomicCAS(slot + ((first + q) & (kBucketSlots - 1)), kEmptySlot, key);
             if (old == kEmptySlot || old == key) return true;
         }
         b = (b + 1) & mask;
@@ -810,7 +811,7 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         }
         g->eset_pending = true;
         const uint64_t eset_mask = static_cast<uint64_t>(L.eset_buckets - 1);
-        PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * 4 * L.eset_buckets, es));
+        PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * kBucketSlots * L.eset_buckets, es));
         int64_t eb = (L.m_cap + 255) / 256;
         if (eb > (int64_t)sms * 32) eb = (int64_t)sms * 32;
         if (eb < 1) eb = 1;
