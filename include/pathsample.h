@@ -240,6 +240,34 @@ int ps_batch_sample_prepared(const void *d_table, int32_t n_graphs, const ps_wor
                              int64_t n_items, uint64_t *d_hist, uint32_t *d_counter,
                              const ps_tuning *t, ps_stream_t stream);
 
+/* ---------------------------------------------------------- exact counts */
+
+/* Exact counts by enumeration, the ground truth that sampled estimates are
+ * checked against where brute force is out of reach.  The paper obtains its
+ * exact counts with separate enumeration code (Section 6) and does not
+ * describe it; this call computes the non-induced counts N_1..N_6 of Eq. (1)
+ * and inverts Eq. (1) for the induced counts C_1..C_6:
+ *   N_1 = sum_v C(d_v, 3), N_2 = W - 3T (W counts each 3-path once and each
+ *   triangle three times, Section 3), N_3 = sum over triangles of
+ *   (d_a + d_b + d_c - 6), N_4 = 4-cycles, N_5 = sum over edges of
+ *   C(t_e, 2) (t_e = triangles through e), N_6 = 4-cliques.
+ * g must have been through ps_tau_prefix (it uses the canonical graph, W,
+ * N_1 and g's adjacency test).  Work: one hash-set test per upper-part entry
+ * of the lower endpoint of every edge, plus one per pair of common upper
+ * neighbours (4-cliques), plus the wedges below each vertex (4-cycles).
+ *
+ * d_scratch: device, 256-byte aligned, at least
+ * ps_exact_scratch_bytes(g, 1) bytes; ps_exact_scratch_bytes(g, 0) is the
+ * size that lets the 4-cycle pass run on two blocks per SM (each block needs
+ * 4 n bytes of counters).  On return its first 4 m bytes hold t_e (uint32,
+ * edge order of PS_ARRAY_EDGES).  N (uint64 [6]) and C (int64 [6]) are host
+ * arrays.  Synchronises `stream`.  Returns PS_ERR_STATE before
+ * ps_tau_prefix, PS_ERR_WORKSPACE for a missing, misaligned or too small
+ * scratch, PS_ERR_OVERFLOW when a count does not fit its type. */
+size_t ps_exact_scratch_bytes(const ps_graph *g, int max_blocks);
+int ps_count_exact(const ps_graph *g, void *d_scratch, size_t scratch_bytes, ps_stream_t stream,
+                   uint64_t N[6], int64_t C[6]);
+
 /* ------------------------------------------------------ allocation-free */
 
 /* The paper has no counterpart to this call.  It is the exact prefix scan

@@ -107,6 +107,7 @@ def _load():
                                 I32),
                 "or_bruteforce_counts": ([I64, V, V, V], I32),
                 "or_exact_counts": ([I64, V, V, V, V], I32),
+                "or_triangles_per_edge": ([I64, V, V, I64, V, V, V], I32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -334,6 +335,19 @@ def bruteforce_counts(off, col) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"or_bruteforce_counts: {rc}")
     return C.astype(np.int64)
+
+
+def triangles_per_edge(off, col, eu, ev) -> np.ndarray:
+    """|N(u) ∩ N(v)| for each given edge (u, v); rows must be sorted."""
+    off, col = _csr(off, col)
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    t = np.zeros(eu.shape[0], dtype=np.uint32)
+    rc = _load().or_triangles_per_edge(off.shape[0] - 1, _p(off), _p(col), eu.shape[0], _p(eu),
+                                       _p(ev), _p(t))
+    if rc != 0:
+        raise ValueError(f"or_triangles_per_edge: {rc}")
+    return t
 
 
 def exact_counts(off, col):

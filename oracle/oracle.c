@@ -572,6 +572,21 @@ static int64_t intersect_count(const int32_t *a, int64_t la, const int32_t *b, i
     return c;
 }
 
+/* Triangles through each edge: t_j = |N(u_j) ∩ N(v_j)| for the edges (u_j,
+ * v_j) given (the per-edge counts whose pairs make the chordal 4-cycles of
+ * Eq. (1): a chordal 4-cycle is two triangles sharing its chord).  Rows must
+ * be sorted ascending. */
+int or_triangles_per_edge(int64_t n, const int64_t *off, const int32_t *col, int64_t m,
+                          const int32_t *eu, const int32_t *ev, uint32_t *t) {
+    for (int64_t j = 0; j < m; j++) {
+        const int64_t u = eu[j], v = ev[j];
+        if (u < 0 || u >= n || v < 0 || v >= n) return OR_ERR_ARG;
+        t[j] = (uint32_t)intersect_count(col + off[u], off[u + 1] - off[u], col + off[v],
+                                         off[v + 1] - off[v]);
+    }
+    return OR_OK;
+}
+
 /* Exact induced counts from non-induced ones through Eq. (1).  On a graph
  * with sorted rows:
  *   N1 = sum_v C(d_v, 3)                   3-stars

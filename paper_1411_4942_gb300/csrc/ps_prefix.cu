@@ -39,28 +39,6 @@ struct StorePrefix {
     }
 };
 
-__device__ __forceinline__ void add128(uint64_t &lo, uint64_t &hi, uint64_t x) {
-    lo += x;
-    hi += (lo < x);
-}
-
-__device__ __forceinline__ void atomic_add128(u64 *pair, uint64_t lo, uint64_t hi) {
-    const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long *>(pair),
-                                             static_cast<unsigned long long>(lo));
-    if (old + lo < old) hi += 1;
-    if (hi) atomicAdd(reinterpret_cast<unsigned long long *>(pair + 1), static_cast<unsigned long long>(hi));
-}
-
-__device__ __forceinline__ void warp_add128(uint64_t &lo, uint64_t &hi) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t l2 = __shfl_down_sync(0xffffffffu, lo, o);
-        const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
-        add128(lo, hi, l2);
-        hi += h2;
-    }
-}
-
 // N_1 = sum_v C(d_v, 3) (128-bit) and the number of hub rows: the top
 // `hub_cap` labels whose degree is at least kHubMinDegree.
 __global__ void __launch_bounds__(256)

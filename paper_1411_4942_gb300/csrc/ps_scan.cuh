@@ -1,5 +1,6 @@
-// ps_scan.cuh -- warp utilities and the single-pass decoupled look-back
-// scan used by the load and prefix steps (not by the sampling kernels).
+// ps_scan.cuh -- warp utilities, 128-bit accumulation and the single-pass
+// decoupled look-back scan used by the load, prefix and exact-count steps
+// (not by the sampling kernels).
 #pragma once
 
 #include "ps_device.cuh"
@@ -54,6 +55,30 @@ struct OpMax {
     template <typename T>
     __device__ __forceinline__ T operator()(T x, T y) const { return x > y ? x : y; }
 };
+
+// ------------------------------------------------ 128-bit accumulation
+
+__device__ __forceinline__ void add128(uint64_t &lo, uint64_t &hi, uint64_t x) {
+    lo += x;
+    hi += (lo < x);
+}
+
+__device__ __forceinline__ void atomic_add128(u64 *pair, uint64_t lo, uint64_t hi) {
+    const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long *>(pair),
+                                             static_cast<unsigned long long>(lo));
+    if (old + lo < old) hi += 1;
+    if (hi) atomicAdd(reinterpret_cast<unsigned long long *>(pair + 1), static_cast<unsigned long long>(hi));
+}
+
+__device__ __forceinline__ void warp_add128(uint64_t &lo, uint64_t &hi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const uint64_t h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        add128(lo, hi, l2);
+        hi += h2;
+    }
+}
 
 // ------------------------------------------------ decoupled look-back scan
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "ps_sample_centered", "ps_estimate", "ps_graph_free", "ps_strerror", "ps_graph_copy",
     "ps_end_to_end_workspace_bytes", "ps_count_motifs_host", "ps_batch_table_bytes",
     "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared", "ps_kernel_launches",
+    "ps_exact_scratch_bytes", "ps_count_exact",
 ]
 
 
@@ -113,6 +114,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_kernel_launches": ([], U64),
             "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
             "ps_selftest_bounded_wait": ([V, ctypes.c_uint32, V], I32),
+            "ps_exact_scratch_bytes": ([V, I32], SZ),
+            "ps_count_exact": ([V, V, SZ, V, V, V], I32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -233,6 +236,19 @@ def ps_prefix_pairs_static(d_a, d_b, d_pa, d_pb, count: int, stream=None) -> int
                                                      _stream_ptr(stream)))
 
 
+def ps_exact_scratch_bytes(handle, max_blocks: int = 0) -> int:
+    return int(load_library().ps_exact_scratch_bytes(handle, max_blocks))
+
+
+def ps_count_exact(handle, d_scratch: int, nbytes: int, stream=None):
+    """Exact counts; returns (status, N uint64[6], C int64[6])."""
+    N = np.zeros(6, dtype=np.uint64)
+    C = np.zeros(6, dtype=np.int64)
+    rc = load_library().ps_count_exact(handle, d_scratch, nbytes, _stream_ptr(stream),
+                                       N.ctypes.data, C.ctypes.data)
+    return int(rc), N, C
+
+
 def ps_batch_table_bytes(n_graphs: int) -> int:
     return int(load_library().ps_batch_table_bytes(n_graphs))
 
@@ -341,6 +357,21 @@ class Graph:
         rc = ps_graph_copy(self.handle, which, out.ctypes.data, out.nbytes)
         _check(rc, "ps_graph_copy")
         return out
+
+    def count_exact(self, max_blocks: int = 0, stream=None):
+        """Exact counts of the graph: (N1..N6 non-induced, C1..C6 induced, t_e
+        per edge as an int32 device tensor in edge order)."""
+        import torch
+        nbytes = ps_exact_scratch_bytes(self.handle, max_blocks)
+        if nbytes == 0:
+            raise PathSampleError(PS_ERR_STATE, "ps_exact_scratch_bytes")
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        rc, N, C = ps_count_exact(self.handle, scratch.data_ptr(), nbytes, stream)
+        _check(rc, "ps_count_exact")
+        m = int(self.stats.m)
+        te = scratch[: 4 * m].view(torch.int32) if m else torch.zeros(0, dtype=torch.int32,
+                                                                       device=self.device)
+        return N, C, te
 
     def estimate(self, hist6, k3, hist4, kc, delta=0.01):
         h6 = np.asarray(hist6.cpu().numpy() if hasattr(hist6, "cpu") else hist6)[:6]

@@ -302,6 +302,42 @@ def test_exact_counts_match_bruteforce():
         assert np.array_equal(O.EQ1_MATRIX @ C, N)
 
 
+def _edge_triangles(g):
+    og = O.prepare(g.off, g.col)
+    return og, O.triangles_per_edge(og.off, og.col, og.eu, og.ev).astype(np.int64)
+
+
+def test_triangles_per_edge_closed_forms():
+    for n in (3, 4, 7):
+        _, t = _edge_triangles(gg.complete(n))
+        assert (t == n - 2).all()
+    for n in (4, 5, 9):
+        _, t = _edge_triangles(gg.cycle(n))
+        assert (t == 0).all()
+    k = 6  # wheel: hub 0 joined to the rim cycle 1..k
+    pairs = [(0, i) for i in range(1, k + 1)] + [(i, i % k + 1) for i in range(1, k + 1)]
+    og, t = _edge_triangles(gg.from_pairs(k + 1, pairs))
+    hub = og.rank[0]
+    spoke = (og.eu == hub) | (og.ev == hub)
+    assert (t[spoke] == 2).all() and (t[~spoke] == 1).all()
+
+
+def test_triangles_per_edge_bruteforce():
+    rs = np.random.Generator(np.random.PCG64(11))
+    for trial in range(12):
+        n = int(rs.integers(6, 40))
+        g = gg.gnp(n, float(rs.uniform(0.1, 0.7)), 900 + trial)
+        og, t = _edge_triangles(g)
+        A = np.zeros((n, n), dtype=np.int64)
+        for v in range(n):
+            A[v, og.col[og.off[v]:og.off[v + 1]]] = 1
+        common = np.array([sum(A[u, w] * A[v, w] for w in range(n)) for u, v in zip(og.eu, og.ev)])
+        assert np.array_equal(t, common)
+        assert int(t.sum()) == 3 * _triangles(g)
+        N, _ = O.exact_counts(og.off, og.col)
+        assert int(N[4]) == int((t * (t - 1) // 2).sum())  # chordal 4-cycles: triangle pairs
+
+
 # -------------------------------------------------------- closed forms
 
 def _run(g, k=4000, seed=7):
