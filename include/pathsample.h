@@ -149,6 +149,34 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
                 const uint64_t hist4[4], uint64_t kc, double delta, double est[6],
                 double lo[6], double hi[6]);
 
+/* ps_estimate with options.  PS_EST_C1_FROM_CENTRED: C1 = N_1 - C3 - 2 C5 -
+ * 4 C6 takes C5 and C6 (and their bars) from the centred sampler instead of
+ * the 3-path sampler (C3 only the 3-path sampler sees).  The paper leaves
+ * the choice open: Alg. 2 states the identity inside the 3-path algorithm,
+ * while the end of Section 4 reports C4..C6 from the centred one.  Unknown
+ * flag bits: PS_ERR_ARG. */
+#define PS_EST_C1_FROM_CENTRED 1u
+int ps_estimate_ex(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
+                   const uint64_t hist4[4], uint64_t kc, double delta, uint32_t flags,
+                   double est[6], double lo[6], double hi[6]);
+
+/* Sampling until the error bars are narrow enough (the paper fixes k in
+ * advance; this stops early from the same Corollary 5.3 bars).  Both samplers
+ * draw ids [0, k) for k = k0, 2 k0, 4 k0, ... (capped at k_max, the last
+ * look); after each look the estimates use confidence delta / L, L the number
+ * of looks the schedule allows, so the union bound keeps the final bars at
+ * confidence >= 1 - delta despite the early stop.  It stops at the first k
+ * where every motif i (1..6) with bit i-1 of motif_mask set has
+ * max(hi - est, est - lo) <= target * |est|, or at k_max.  d_hist6 /
+ * d_hist4: device uint64 [6] / [4], zeroed by the call; the final
+ * histograms equal one ps_sample_* call of k_used ids.  flags as in
+ * ps_estimate_ex.  Synchronises `stream` after every look.  Returns
+ * ps_estimate's status (PS_NO_PATHS stops after the first look). */
+int ps_count_adaptive(const ps_graph *g, uint64_t seed, double target, double delta, uint64_t k0,
+                      uint64_t k_max, uint32_t motif_mask, uint32_t flags, uint64_t *d_hist6,
+                      uint64_t *d_hist4, ps_stream_t stream, uint64_t *k_used, uint64_t hist6[6],
+                      uint64_t hist4[4], double est[6], double lo[6], double hi[6]);
+
 /* Releases the host metadata of g (not the workspace, which the caller owns),
  * first waiting for library work that may still write into the workspace
  * (the hash set build of ps_load_csr); work the caller queued on its own

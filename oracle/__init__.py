@@ -105,6 +105,8 @@ def _load():
                 "or_chernoff_bounds": ([U64, U64, ctypes.c_double, V, V], None),
                 "or_estimate": ([U64, U64, U64, U64, V, U64, V, U64, ctypes.c_double, V, V, V],
                                 I32),
+                "or_estimate_ex": ([U64, U64, U64, U64, V, U64, V, U64, ctypes.c_double, I32, V, V,
+                                    V], I32),
                 "or_bruteforce_counts": ([I64, V, V, V], I32),
                 "or_exact_counts": ([I64, V, V, V, V], I32),
                 "or_triangles_per_edge": ([I64, V, V, I64, V, V, V], I32),
@@ -317,14 +319,45 @@ def chernoff_bounds(count: int, k: int, delta: float):
 
 
 def estimate(W: int, Lambda: int, N1: int, hist6, k3: int, hist4, kc: int,
-             delta: float = 0.01):
-    """Estimates and error bars of all six induced counts (motif 1..6)."""
+             delta: float = 0.01, c1_from_centred: bool = False):
+    """Estimates and error bars of all six induced counts (motif 1..6);
+    c1_from_centred feeds C1 with the centred sampler's C5 and C6."""
     h6 = np.ascontiguousarray(hist6, dtype=np.uint64)
     h4 = np.ascontiguousarray(hist4, dtype=np.uint64)
     est, lo, hi = (np.zeros(6), np.zeros(6), np.zeros(6))
-    st = _load().or_estimate(W, Lambda, N1 & ((1 << 64) - 1), N1 >> 64, _p(h6), k3, _p(h4), kc,
-                             delta, _p(est), _p(lo), _p(hi))
+    st = _load().or_estimate_ex(W, Lambda, N1 & ((1 << 64) - 1), N1 >> 64, _p(h6), k3, _p(h4), kc,
+                                delta, int(bool(c1_from_centred)), _p(est), _p(lo), _p(hi))
     return int(st), est, lo, hi
+
+
+def adaptive(g: OracleGraph, seed: int, target: float, delta: float, k0: int, k_max: int,
+             motif_mask: int = 0x3F, c1_from_centred: bool = False, threads: int = 1):
+    """Sampling until the Corollary 5.3 bars are narrow: both samplers over ids
+    [0, k) for k = k0, 2 k0, ... capped at k_max; every look's bars at
+    delta / (number of looks the schedule allows), so the union bound holds
+    over the early stop; stops when every selected motif i has
+    max(hi - est, est - lo) <= target * |est|, or at k_max.
+    Returns (k, hist6, hist4, est, lo, hi, status)."""
+    looks, k = 1, k0
+    while k < k_max:
+        k = k_max if k > k_max // 2 else 2 * k
+        looks += 1
+    h6 = np.zeros(6, dtype=np.uint64)
+    h4 = np.zeros(4, dtype=np.uint64)
+    done, k = 0, k0
+    while True:
+        if g.W > 0:
+            h6 += sample_3paths(g, k - done, seed, done, threads)
+        if g.Lambda > 0:
+            h4 += sample_centered(g, k - done, seed, done, threads)
+        done = k
+        st, est, lo, hi = estimate(g.W, g.Lambda, g.N1, h6, k, h4, k, delta / looks,
+                                   c1_from_centred)
+        met = all(max(hi[i] - est[i], est[i] - lo[i]) <= target * abs(est[i])
+                  for i in range(6) if (motif_mask >> i) & 1)
+        if met or st == NO_PATHS or k == k_max:
+            return done, h6, h4, est, lo, hi, st
+        k = k_max if k > k_max // 2 else 2 * k
 
 
 def bruteforce_counts(off, col) -> np.ndarray:

@@ -482,9 +482,23 @@ void or_chernoff_bounds(uint64_t count, uint64_t k, double delta, double *pl, do
 static const double A2[7] = {0, 0, 1, 2, 4, 6, 12}; /* 3-paths per motif, Eq. (1) row 2 */
 static const double B[7] = {0, 0, 0, 0, 1, 1, 3};   /* centred 3-paths, Lemma 4.2 */
 
+/* c1_from_centred != 0 takes C5 and C6 in the 3-star identity C1 = N1 - C3 -
+ * 2 C5 - 4 C6 (Alg. 2) from the centred sampler (Alg. 4) instead of the
+ * 3-path sampler, with their bars; C3 always comes from the 3-path sampler,
+ * the only one that sees tailed triangles. */
+int or_estimate_ex(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
+                   const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
+                   double delta, int c1_from_centred, double est[6], double lo[6], double hi[6]);
+
 int or_estimate(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
                 const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
                 double delta, double est[6], double lo[6], double hi[6]) {
+    return or_estimate_ex(W, Lambda, n1_lo, n1_hi, hist6, k3, hist4, kc, delta, 0, est, lo, hi);
+}
+
+int or_estimate_ex(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
+                   const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
+                   double delta, int c1_from_centred, double est[6], double lo[6], double hi[6]) {
     if (k3 == 0 || kc == 0 || !(delta > 0.0 && delta < 1.0)) return OR_ERR_ARG;
     double n1 = (double)(((u128)n1_hi << 64) | (u128)n1_lo);
     double basic[7] = {0}, blo[7] = {0}, bhi[7] = {0};
@@ -497,9 +511,23 @@ int or_estimate(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
         blo[i] = pl * K;
         bhi[i] = pu * K;
     }
-    double c1 = n1 - basic[3] - 2.0 * basic[5] - 4.0 * basic[6];
-    double down = (basic[3] - blo[3]) + 2.0 * (basic[5] - blo[5]) + 4.0 * (basic[6] - blo[6]);
-    double up = (bhi[3] - basic[3]) + 2.0 * (bhi[5] - basic[5]) + 4.0 * (bhi[6] - basic[6]);
+    double cen[7] = {0}, clo[7] = {0}, chi[7] = {0};
+    for (int i = 4; i <= 6; i++) {
+        if (Lambda == 0) continue;
+        double K = (double)Lambda / B[i];
+        cen[i] = (double)hist4[i - 3] * (double)Lambda / (double)kc / B[i];
+        double pl, pu;
+        or_chernoff_bounds(hist4[i - 3], kc, delta, &pl, &pu);
+        clo[i] = pl * K;
+        chi[i] = pu * K;
+    }
+    /* C5 and C6 of the 3-star identity: the 3-path sampler's by default */
+    const double *e = c1_from_centred ? cen : basic;
+    const double *el = c1_from_centred ? clo : blo;
+    const double *eh = c1_from_centred ? chi : bhi;
+    double c1 = n1 - basic[3] - 2.0 * e[5] - 4.0 * e[6];
+    double down = (basic[3] - blo[3]) + 2.0 * (e[5] - el[5]) + 4.0 * (e[6] - el[6]);
+    double up = (bhi[3] - basic[3]) + 2.0 * (eh[5] - e[5]) + 4.0 * (eh[6] - e[6]);
     est[0] = c1;
     lo[0] = c1 - up;
     hi[0] = c1 + down;
@@ -509,16 +537,9 @@ int or_estimate(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
         hi[i - 1] = bhi[i];
     }
     for (int i = 4; i <= 6; i++) {
-        if (Lambda == 0) {
-            est[i - 1] = lo[i - 1] = hi[i - 1] = 0.0;
-            continue;
-        }
-        double K = (double)Lambda / B[i];
-        est[i - 1] = (double)hist4[i - 3] * (double)Lambda / (double)kc / B[i];
-        double pl, pu;
-        or_chernoff_bounds(hist4[i - 3], kc, delta, &pl, &pu);
-        lo[i - 1] = pl * K;
-        hi[i - 1] = pu * K;
+        est[i - 1] = cen[i];
+        lo[i - 1] = clo[i];
+        hi[i - 1] = chi[i];
     }
     return (W == 0 || Lambda == 0) ? OR_NO_PATHS : OR_OK;
 }

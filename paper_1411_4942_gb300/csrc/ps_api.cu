@@ -321,13 +321,20 @@ int ps_sample_centered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t fi
 
 int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4],
                 uint64_t kc, double delta, double est[6], double lo[6], double hi[6]) {
+    return ps_estimate_ex(st, hist6, k3, hist4, kc, delta, 0u, est, lo, hi);
+}
+
+int ps_estimate_ex(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4],
+                   uint64_t kc, double delta, uint32_t flags, double est[6], double lo[6], double hi[6]) {
     if (!st || !hist6 || !hist4 || !est || !lo || !hi) return PS_ERR_ARG;
     if (k3 == 0 || kc == 0 || !(delta > 0.0 && delta < 1.0)) return PS_ERR_ARG;
+    if (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED)) return PS_ERR_ARG;
     // 3-paths per motif (row 2 of Eq. (1)) and centred 3-paths (Lemma 4.2)
     static const double kA2[7] = {0, 0, 1, 2, 4, 6, 12};
     static const double kB[7] = {0, 0, 0, 0, 1, 1, 3};
     const unsigned __int128 n1w = (static_cast<unsigned __int128>(st->N1_hi) << 64) | st->N1_lo;
     const double n1 = static_cast<double>(n1w);
+    // Alg. 2: every motif with a 3-path, from the 3-path sampler
     double c[7] = {0}, clo[7] = {0}, chi[7] = {0};
     if (st->W > 0) {
         for (int i = 2; i <= 6; i++) {
@@ -339,10 +346,26 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const 
             chi[i] = pu * scale;
         }
     }
-    // Alg. 2: induced 3-stars from N_1 and the 3-path sampler's terms
-    const double c1 = n1 - c[3] - 2.0 * c[5] - 4.0 * c[6];
-    const double below = (c[3] - clo[3]) + 2.0 * (c[5] - clo[5]) + 4.0 * (c[6] - clo[6]);
-    const double above = (chi[3] - c[3]) + 2.0 * (chi[5] - c[5]) + 4.0 * (chi[6] - c[6]);
+    // Alg. 4: the cycle-based motifs from the centred sampler
+    double q[7] = {0}, qlo[7] = {0}, qhi[7] = {0};
+    if (st->Lambda > 0) {
+        for (int i = 4; i <= 6; i++) {
+            q[i] = static_cast<double>(hist4[i - 3]) * static_cast<double>(st->Lambda) / static_cast<double>(kc) / kB[i];
+            double pl, pu;
+            binomial_bar(hist4[i - 3], kc, delta, &pl, &pu);
+            const double scale = static_cast<double>(st->Lambda) / kB[i];
+            qlo[i] = pl * scale;
+            qhi[i] = pu * scale;
+        }
+    }
+    // Alg. 2's induced 3-stars: N_1 - C_3 - 2 C_5 - 4 C_6, with C_5 and C_6 from
+    // the 3-path sampler unless the flag asks for the centred ones (C_3 only
+    // the 3-path sampler sees)
+    const bool cen = (flags & PS_EST_C1_FROM_CENTRED) != 0;
+    const double *e = cen ? q : c, *el = cen ? qlo : clo, *eh = cen ? qhi : chi;
+    const double c1 = n1 - c[3] - 2.0 * e[5] - 4.0 * e[6];
+    const double below = (c[3] - clo[3]) + 2.0 * (e[5] - el[5]) + 4.0 * (e[6] - el[6]);
+    const double above = (chi[3] - c[3]) + 2.0 * (eh[5] - e[5]) + 4.0 * (eh[6] - e[6]);
     est[0] = c1;
     lo[0] = c1 - above;
     hi[0] = c1 + below;
@@ -351,21 +374,61 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const 
         lo[i - 1] = clo[i];
         hi[i - 1] = chi[i];
     }
-    // Alg. 4: cycle-based motifs from the centred sampler
+    // the final combination (end of Section 4): C_4..C_6 from Alg. 4
     for (int i = 4; i <= 6; i++) {
-        if (st->Lambda == 0) {
-            est[i - 1] = lo[i - 1] = hi[i - 1] = 0.0;
-            continue;
-        }
-        est[i - 1] = static_cast<double>(hist4[i - 3]) * static_cast<double>(st->Lambda) /
-                     static_cast<double>(kc) / kB[i];
-        double pl, pu;
-        binomial_bar(hist4[i - 3], kc, delta, &pl, &pu);
-        const double scale = static_cast<double>(st->Lambda) / kB[i];
-        lo[i - 1] = pl * scale;
-        hi[i - 1] = pu * scale;
+        est[i - 1] = q[i];
+        lo[i - 1] = qlo[i];
+        hi[i - 1] = qhi[i];
     }
     return (st->W == 0 || st->Lambda == 0) ? PS_NO_PATHS : PS_OK;
+}
+
+// Looks of the doubling schedule k0, 2 k0, 4 k0, ..., capped at k_max.
+static int adaptive_looks(uint64_t k0, uint64_t k_max) {
+    int r = 1;
+    for (uint64_t k = k0; k < k_max; k = (k > k_max / 2) ? k_max : 2 * k) r++;
+    return r;
+}
+
+int ps_count_adaptive(const ps_graph *g, uint64_t seed, double target, double delta, uint64_t k0,
+                      uint64_t k_max, uint32_t motif_mask, uint32_t flags, uint64_t *d_hist6,
+                      uint64_t *d_hist4, ps_stream_t stream, uint64_t *k_used, uint64_t hist6[6],
+                      uint64_t hist4[4], double est[6], double lo[6], double hi[6]) {
+    if (!g || !d_hist6 || !d_hist4 || !k_used || !hist6 || !hist4 || !est || !lo || !hi) return PS_ERR_ARG;
+    if (!g->prefixed) return PS_ERR_STATE;
+    if (k0 == 0 || k_max < k0 || !(target > 0.0) || !(delta > 0.0 && delta < 1.0)) return PS_ERR_ARG;
+    if ((motif_mask & ~0x3fu) != 0 || (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED))) return PS_ERR_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PS_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PS_CUDA_TRY(cudaMemsetAsync(d_hist6, 0, 6 * sizeof(uint64_t), s));
+    PS_CUDA_TRY(cudaMemsetAsync(d_hist4, 0, 4 * sizeof(uint64_t), s));
+    // the caller's confidence is split evenly over the looks (union bound)
+    const double delta_look = delta / static_cast<double>(adaptive_looks(k0, k_max));
+    uint64_t done = 0, k = k0;
+    int rc = PS_OK;
+    while (true) {
+        const uint64_t add = k - done;
+        if (g->stats.W > 0) rc = launch_sampler(g, 0, add, seed, done, d_hist6, s);
+        if (rc == PS_OK && g->stats.Lambda > 0) rc = launch_sampler(g, 1, add, seed, done, d_hist4, s);
+        if (rc != PS_OK) return rc;
+        PS_CUDA_TRY(cudaMemcpyAsync(hist6, d_hist6, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        PS_CUDA_TRY(cudaMemcpyAsync(hist4, d_hist4, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        PS_CUDA_TRY(cudaStreamSynchronize(s));
+        done = k;
+        rc = ps_estimate_ex(&g->stats, hist6, k, hist4, k, delta_look, flags, est, lo, hi);
+        if (rc != PS_OK && rc != PS_NO_PATHS) return rc;
+        bool met = true;
+        for (int i = 0; i < 6; i++)
+            if (motif_mask & (1u << i)) {
+                const double half = std::fmax(hi[i] - est[i], est[i] - lo[i]);
+                met = met && half <= target * std::fabs(est[i]);
+            }
+        if (met || rc == PS_NO_PATHS || k == k_max) break;
+        k = (k > k_max / 2) ? k_max : 2 * k;
+    }
+    *k_used = done;
+    return rc;
 }
 
 void ps_graph_free(ps_graph *g) { delete g; }

@@ -29,8 +29,10 @@ EXPORTED = [
     "ps_sample_centered", "ps_estimate", "ps_graph_free", "ps_strerror", "ps_graph_copy",
     "ps_end_to_end_workspace_bytes", "ps_count_motifs_host", "ps_batch_table_bytes",
     "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared", "ps_kernel_launches",
-    "ps_exact_scratch_bytes", "ps_count_exact",
+    "ps_exact_scratch_bytes", "ps_count_exact", "ps_estimate_ex", "ps_count_adaptive",
 ]
+
+PS_EST_C1_FROM_CENTRED = 1
 
 
 class PathSampleError(RuntimeError):
@@ -115,6 +117,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
             "ps_selftest_bounded_wait": ([V, ctypes.c_uint32, V], I32),
             "ps_exact_scratch_bytes": ([V, I32], SZ),
+            "ps_estimate_ex": ([P(PsStats), V, U64, V, U64, ctypes.c_double, ctypes.c_uint32, V, V,
+                                V], I32),
+            "ps_count_adaptive": ([V, U64, ctypes.c_double, ctypes.c_double, U64, U64, ctypes.c_uint32,
+                                   ctypes.c_uint32, V, V, V, P(U64), V, V, V, V, V], I32),
             "ps_count_exact": ([V, V, SZ, V, V, V], I32),
         }
         for name, (args, res) in sig.items():
@@ -188,6 +194,32 @@ def ps_estimate(stats: PsStats, hist6, k3: int, hist4, kc: int, delta: float = 0
     rc = load_library().ps_estimate(ctypes.byref(stats), h6.ctypes.data, k3, h4.ctypes.data, kc,
                                     delta, est.ctypes.data, lo.ctypes.data, hi.ctypes.data)
     return int(rc), est, lo, hi
+
+
+def ps_estimate_ex(stats: PsStats, hist6, k3: int, hist4, kc: int, delta: float = 0.01,
+                   flags: int = 0):
+    h6 = np.ascontiguousarray(hist6, dtype=np.uint64)
+    h4 = np.ascontiguousarray(hist4, dtype=np.uint64)
+    est, lo, hi = np.zeros(6), np.zeros(6), np.zeros(6)
+    rc = load_library().ps_estimate_ex(ctypes.byref(stats), h6.ctypes.data, k3, h4.ctypes.data, kc,
+                                       delta, flags, est.ctypes.data, lo.ctypes.data,
+                                       hi.ctypes.data)
+    return int(rc), est, lo, hi
+
+
+def ps_count_adaptive(handle, seed: int, target: float, delta: float, k0: int, k_max: int,
+                      d_hist6: int, d_hist4: int, motif_mask: int = 0x3F, flags: int = 0,
+                      stream=None):
+    """Returns (status, k_used, hist6, hist4, est, lo, hi)."""
+    k_used = ctypes.c_uint64(0)
+    h6 = np.zeros(6, dtype=np.uint64)
+    h4 = np.zeros(4, dtype=np.uint64)
+    est, lo, hi = np.zeros(6), np.zeros(6), np.zeros(6)
+    rc = load_library().ps_count_adaptive(handle, seed, target, delta, k0, k_max, motif_mask, flags,
+                                          d_hist6, d_hist4, _stream_ptr(stream), ctypes.byref(k_used),
+                                          h6.ctypes.data, h4.ctypes.data, est.ctypes.data,
+                                          lo.ctypes.data, hi.ctypes.data)
+    return int(rc), int(k_used.value), h6, h4, est, lo, hi
 
 
 def ps_graph_free(handle) -> None:
@@ -372,6 +404,17 @@ class Graph:
         te = scratch[: 4 * m].view(torch.int32) if m else torch.zeros(0, dtype=torch.int32,
                                                                        device=self.device)
         return N, C, te
+
+    def count_adaptive(self, seed: int, target: float, delta: float = 0.01, k0: int = 1 << 16,
+                       k_max: int = 1 << 26, motif_mask: int = 0x3F, c1_from_centred: bool = False,
+                       stream=None):
+        """Samples until the bars are narrow; (k_used, hist6, hist4, est, lo, hi)."""
+        h6, h4 = self.new_hist(), self.new_hist()
+        rc, k, a, b, est, lo, hi = ps_count_adaptive(
+            self.handle, seed, target, delta, k0, k_max, h6.data_ptr(), h4.data_ptr(), motif_mask,
+            PS_EST_C1_FROM_CENTRED if c1_from_centred else 0, stream)
+        _check(rc, "ps_count_adaptive", (PS_OK, PS_NO_PATHS))
+        return k, a, b, est, lo, hi
 
     def estimate(self, hist6, k3, hist4, kc, delta=0.01):
         h6 = np.asarray(hist6.cpu().numpy() if hasattr(hist6, "cpu") else hist6)[:6]

@@ -447,6 +447,53 @@ def test_ideal_histograms_give_exact_counts():
         c4 = O.enumerate_centered(og)
         st, est, lo, hi = O.estimate(og.W, og.Lambda, og.N1, c6, og.W, c4, og.Lambda)
         assert np.allclose(est, C, rtol=1e-12, atol=1e-9)
+        # the centred-fed 3-star identity is exact on exact inputs too
+        st, est, lo, hi = O.estimate(og.W, og.Lambda, og.N1, c6, og.W, c4, og.Lambda,
+                                     c1_from_centred=True)
+        assert np.allclose(est, C, rtol=1e-12, atol=1e-9)
+
+
+def test_c1_variant_changes_only_c1():
+    g = gg.gnp(40, 0.3, 12)
+    og = O.prepare(g.off, g.col)
+    h6, h4 = O.sample_3paths(og, 20000, 3), O.sample_centered(og, 20000, 3)
+    _, a, alo, ahi = O.estimate(og.W, og.Lambda, og.N1, h6, 20000, h4, 20000)
+    _, b, blo, bhi = O.estimate(og.W, og.Lambda, og.N1, h6, 20000, h4, 20000, c1_from_centred=True)
+    assert np.array_equal(a[1:], b[1:]) and np.array_equal(alo[1:], blo[1:])
+    assert a[0] != b[0]
+
+
+# ------------------------------------------------------- adaptive sample size
+
+def test_adaptive_schedule_and_stop_rule():
+    g = gg.chung_lu(400, 8.0, 2.4, 60.0, 9)
+    og = O.prepare(g.off, g.col)
+    k0, k_max, delta, target = 1 << 10, 1 << 17, 0.01, 0.05
+    k, h6, h4, est, lo, hi, st = O.adaptive(og, 5, target, delta, k0, k_max, motif_mask=0b11)
+    # the histograms equal one run of k ids
+    assert np.array_equal(h6, O.sample_3paths(og, k, 5)) and np.array_equal(h4, O.sample_centered(og, k, 5))
+    # it stopped at the first look of the schedule where C1 and C2 met the target
+    looks = [k0 << i for i in range(8)]  # 2^10 .. 2^17
+    assert k in looks
+    for kk in looks[:looks.index(k) + 1]:
+        _, e, l, h = O.estimate(og.W, og.Lambda, og.N1, O.sample_3paths(og, kk, 5), kk,
+                                O.sample_centered(og, kk, 5), kk, delta / len(looks))
+        met = all(max(h[i] - e[i], e[i] - l[i]) <= target * abs(e[i]) for i in (0, 1))
+        assert met == (kk == k)
+    # unreachable target: runs to k_max; trivial target: stops at k0
+    assert O.adaptive(og, 5, 1e-9, delta, k0, k_max)[0] == k_max
+    assert O.adaptive(og, 5, 1e9, delta, k0, k_max)[0] == k0
+    # k_max not a power-of-two multiple of k0 is the last look
+    assert O.adaptive(og, 5, 1e-9, delta, 1000, 5000)[0] == 5000
+
+
+def test_adaptive_bars_cover_exact_counts():
+    g = gg.gnp(30, 0.35, 41)
+    og = O.prepare(g.off, g.col)
+    C = O.bruteforce_counts(g.off, g.col)
+    for seed in range(6):
+        k, _, _, est, lo, hi, _ = O.adaptive(og, seed, 0.02, 0.01, 1 << 10, 1 << 16)
+        assert ((lo <= C) & (C <= hi)).all(), (seed, k, est, C)
 
 
 # ---------------------------------------------------------- error bars
