@@ -268,6 +268,26 @@ int ps_batch_sample_prepared(const void *d_table, int32_t n_graphs, const ps_wor
                              int64_t n_items, uint64_t *d_hist, uint32_t *d_counter,
                              const ps_tuning *t, ps_stream_t stream);
 
+/* ------------------------------------------------------ edge-list ingest */
+
+/* Section 2's input from a raw edge list, on the device (the paper's
+ * experiments start from edge lists, Section 6).  d_src / d_dst: device int32
+ * [n_edges], edge i = {d_src[i], d_dst[i]}, ids in [0, n); either direction,
+ * repeats and self-loops are allowed.  Writes the undirected simple graph:
+ * self-loops dropped, both arcs of every remaining pair once, rows sorted
+ * ascending -- d_off (device int64 [n + 1]) and d_col (device int32, room
+ * for 2 n_edges entries; the first *nnz are written) -- ready for
+ * ps_load_csr.  d_workspace: device, 256-byte aligned, at least
+ * ps_ingest_workspace_bytes(n, n_edges) bytes (about 20 bytes per edge).
+ * *nnz (host) receives the number of arcs.  Synchronises `stream`.  Returns
+ * PS_ERR_ARG for an id outside [0, n) (or n, n_edges out of range: n < 2^31 - 1,
+ * 2 n_edges < 2^31 - 1), PS_ERR_WORKSPACE for a missing, misaligned or small
+ * workspace. */
+size_t ps_ingest_workspace_bytes(int64_t n, int64_t n_edges);
+int ps_csr_from_edges(int64_t n, int64_t n_edges, const int32_t *d_src, const int32_t *d_dst,
+                      void *d_workspace, size_t ws_bytes, int64_t *d_off, int32_t *d_col,
+                      int64_t *nnz, ps_stream_t stream);
+
 /* ---------------------------------------------------------- exact counts */
 
 /* Exact counts by enumeration, the ground truth that sampled estimates are

@@ -138,6 +138,29 @@ def validate(off, col) -> int:
     return int(_load().or_validate(n, col.shape[0], _p(off), _p(col)))
 
 
+def csr_from_edges(n: int, src, dst):
+    """Section 2's input from a raw edge list: the undirected simple graph on
+    vertices [0, n) with an edge {u, v} for every listed pair with u != v
+    (self-loops dropped, repeats and both directions merged), as (off, col)
+    with both arcs of every edge and each row ascending."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    if src.shape != dst.shape or (src.size and (min(src.min(), dst.min()) < 0 or
+                                                max(src.max(), dst.max()) >= n)):
+        raise ValueError("edge ids outside [0, n)")
+    keep = src != dst
+    a, b = np.minimum(src, dst)[keep], np.maximum(src, dst)[keep]
+    pairs = np.unique(a * n + b)                 # each undirected edge once
+    u, v = pairs // n, pairs % n
+    rows = np.concatenate([u, v])
+    cols = np.concatenate([v, u])
+    order = np.lexsort((cols, rows))             # by row, then column
+    rows, cols = rows[order], cols[order]
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return off, cols.astype(np.int32)
+
+
 def canonicalize(off, col):
     """Section 4 order: returns (rank, coff, ccol) of the relabelled graph."""
     off, col = _csr(off, col)

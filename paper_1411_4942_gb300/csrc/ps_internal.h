@@ -119,6 +119,16 @@ void count_launch();
         PS_CUDA_TRY(cudaGetLastError());        \
     } while (0)
 
+// Stable LSD radix-sort passes of ps_load.cu (8-bit digit at `shift`,
+// uint32 keys with uint32 values, tiles of kRadixTile items): per-tile digit
+// counts stored digit-major, then the scatter after their exclusive scan.
+__global__ void __launch_bounds__(kRadixBlock)
+k_radix_hist(int64_t n, const uint32_t *__restrict__ keys, int shift, uint32_t *counts, int64_t tiles);
+__global__ void __launch_bounds__(kRadixBlock)
+k_radix_scatter(int64_t n, const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int shift,
+                const uint32_t *__restrict__ offsets, int64_t tiles);
+
 // scan helpers (ps_load.cu)
 template <typename T>
 ScanState<T> scan_state(ps_graph *g, int counter_slot);

@@ -30,6 +30,7 @@ EXPORTED = [
     "ps_end_to_end_workspace_bytes", "ps_count_motifs_host", "ps_batch_table_bytes",
     "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared", "ps_kernel_launches",
     "ps_exact_scratch_bytes", "ps_count_exact", "ps_estimate_ex", "ps_count_adaptive",
+    "ps_ingest_workspace_bytes", "ps_csr_from_edges",
 ]
 
 PS_EST_C1_FROM_CENTRED = 1
@@ -117,6 +118,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
             "ps_selftest_bounded_wait": ([V, ctypes.c_uint32, V], I32),
             "ps_exact_scratch_bytes": ([V, I32], SZ),
+            "ps_ingest_workspace_bytes": ([I64, I64], SZ),
+            "ps_csr_from_edges": ([I64, I64, V, V, V, SZ, V, V, P(I64), V], I32),
             "ps_estimate_ex": ([P(PsStats), V, U64, V, U64, ctypes.c_double, ctypes.c_uint32, V, V,
                                 V], I32),
             "ps_count_adaptive": ([V, U64, ctypes.c_double, ctypes.c_double, U64, U64, ctypes.c_uint32,
@@ -279,6 +282,39 @@ def ps_count_exact(handle, d_scratch: int, nbytes: int, stream=None):
     rc = load_library().ps_count_exact(handle, d_scratch, nbytes, _stream_ptr(stream),
                                        N.ctypes.data, C.ctypes.data)
     return int(rc), N, C
+
+
+def ps_ingest_workspace_bytes(n: int, n_edges: int) -> int:
+    return int(load_library().ps_ingest_workspace_bytes(n, n_edges))
+
+
+def ps_csr_from_edges(n: int, n_edges: int, d_src: int, d_dst: int, d_workspace: int, ws_bytes: int,
+                      d_off: int, d_col: int, stream=None):
+    """Returns (status, nnz)."""
+    nnz = ctypes.c_int64(0)
+    rc = load_library().ps_csr_from_edges(n, n_edges, d_src, d_dst, d_workspace, ws_bytes, d_off,
+                                          d_col, ctypes.byref(nnz), _stream_ptr(stream))
+    return int(rc), int(nnz.value)
+
+
+def csr_from_edges(n: int, src, dst, stream=None):
+    """Device CSR (off int64 [n + 1], col int32 [nnz]) of the simple undirected
+    graph listed by the int32 device (or host) arrays src / dst."""
+    import torch
+    dev = src.device if isinstance(src, torch.Tensor) and src.is_cuda else torch.device("cuda")
+    s = torch.as_tensor(src, dtype=torch.int32).to(dev).contiguous()
+    d = torch.as_tensor(dst, dtype=torch.int32).to(dev).contiguous()
+    e = int(s.shape[0])
+    nbytes = ps_ingest_workspace_bytes(n, e)
+    if nbytes == 0:
+        raise PathSampleError(PS_ERR_ARG, "ps_ingest_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(2 * e, 1), dtype=torch.int32, device=dev)
+    rc, nnz = ps_csr_from_edges(n, e, s.data_ptr() if e else None, d.data_ptr() if e else None,
+                                ws.data_ptr(), nbytes, off.data_ptr(), col.data_ptr(), stream)
+    _check(rc, "ps_csr_from_edges")
+    return off, col[:nnz]
 
 
 def ps_batch_table_bytes(n_graphs: int) -> int:

@@ -550,3 +550,36 @@ def test_stored_oracle_values(golden_dir):
         assert O.sample_3paths(og, rec["k"], rec["seed"]).tolist() == rec["hist6"]
         assert O.sample_centered(og, rec["k"], rec["seed"]).tolist() == rec["hist4"]
         assert O.exact_counts(g.off, g.col)[1].tolist() == rec["exact_C"]
+
+
+# --------------------------------------------------------- edge-list ingest
+
+def test_csr_from_edges_closed_form():
+    # K4 listed with repeats, both directions and self-loops
+    src = [0, 1, 2, 3, 0, 1, 3, 2, 2, 0, 1, 0, 3]
+    dst = [1, 0, 3, 2, 2, 3, 0, 1, 2, 3, 1, 1, 3]
+    off, col = O.csr_from_edges(4, src, dst)
+    k4 = gg.complete(4)
+    assert np.array_equal(off, k4.off) and np.array_equal(col, k4.col)
+    off, col = O.csr_from_edges(3, [], [])
+    assert off.tolist() == [0, 0, 0, 0] and col.size == 0
+    with pytest.raises(ValueError):
+        O.csr_from_edges(3, [0], [3])
+
+
+def test_csr_from_edges_matches_generator_and_validates():
+    rs = np.random.Generator(np.random.PCG64(5))
+    for trial in range(10):
+        n = int(rs.integers(1, 300))
+        e = int(rs.integers(0, 4 * n))
+        src = rs.integers(0, n, e)
+        dst = rs.integers(0, n, e)
+        off, col = O.csr_from_edges(n, src, dst)
+        assert O.validate(off, col) == 0
+        keep = src != dst
+        ref = gg.from_pairs(n, np.stack([src[keep], dst[keep]], 1))
+        assert np.array_equal(off, ref.off) and np.array_equal(col, ref.col)
+        # every listed pair is an edge and every edge was listed
+        listed = {(min(a, b), max(a, b)) for a, b in zip(src.tolist(), dst.tolist()) if a != b}
+        got = {(u, int(v)) for u in range(n) for v in col[off[u]:off[u + 1]] if u < v}
+        assert listed == got
