@@ -153,9 +153,13 @@ int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
  * 4 C6 takes C5 and C6 (and their bars) from the centred sampler instead of
  * the 3-path sampler (C3 only the 3-path sampler sees).  The paper leaves
  * the choice open: Alg. 2 states the identity inside the 3-path algorithm,
- * while the end of Section 4 reports C4..C6 from the centred one.  Unknown
- * flag bits: PS_ERR_ARG. */
+ * while the end of Section 4 reports C4..C6 from the centred one.
+ * PS_EST_3PATH_ONLY: report Alg. 2's own estimates of C4..C6 (3-path
+ * sampler) instead of Alg. 4's, e.g. to compare the two samplers (Section 6);
+ * hist4 and kc are then unused but must still be valid.  Unknown flag bits:
+ * PS_ERR_ARG. */
 #define PS_EST_C1_FROM_CENTRED 1u
+#define PS_EST_3PATH_ONLY 2u
 int ps_estimate_ex(const ps_stats *st, const uint64_t hist6[6], uint64_t k3,
                    const uint64_t hist4[4], uint64_t kc, double delta, uint32_t flags,
                    double est[6], double lo[6], double hi[6]);

@@ -342,14 +342,16 @@ def chernoff_bounds(count: int, k: int, delta: float):
 
 
 def estimate(W: int, Lambda: int, N1: int, hist6, k3: int, hist4, kc: int,
-             delta: float = 0.01, c1_from_centred: bool = False):
+             delta: float = 0.01, c1_from_centred: bool = False, three_path_only: bool = False):
     """Estimates and error bars of all six induced counts (motif 1..6);
-    c1_from_centred feeds C1 with the centred sampler's C5 and C6."""
+    c1_from_centred feeds C1 with the centred sampler's C5 and C6;
+    three_path_only reports Alg. 2's own C4..C6 (3-path sampler)."""
     h6 = np.ascontiguousarray(hist6, dtype=np.uint64)
     h4 = np.ascontiguousarray(hist4, dtype=np.uint64)
     est, lo, hi = (np.zeros(6), np.zeros(6), np.zeros(6))
     st = _load().or_estimate_ex(W, Lambda, N1 & ((1 << 64) - 1), N1 >> 64, _p(h6), k3, _p(h4), kc,
-                                delta, int(bool(c1_from_centred)), _p(est), _p(lo), _p(hi))
+                                delta, int(bool(c1_from_centred)) | (2 if three_path_only else 0),
+                                _p(est), _p(lo), _p(hi))
     return int(st), est, lo, hi
 
 

@@ -482,13 +482,14 @@ void or_chernoff_bounds(uint64_t count, uint64_t k, double delta, double *pl, do
 static const double A2[7] = {0, 0, 1, 2, 4, 6, 12}; /* 3-paths per motif, Eq. (1) row 2 */
 static const double B[7] = {0, 0, 0, 0, 1, 1, 3};   /* centred 3-paths, Lemma 4.2 */
 
-/* c1_from_centred != 0 takes C5 and C6 in the 3-star identity C1 = N1 - C3 -
- * 2 C5 - 4 C6 (Alg. 2) from the centred sampler (Alg. 4) instead of the
- * 3-path sampler, with their bars; C3 always comes from the 3-path sampler,
- * the only one that sees tailed triangles. */
+/* flags bit 0: the 3-star identity C1 = N1 - C3 - 2 C5 - 4 C6 (Alg. 2) takes
+ * C5 and C6 from the centred sampler (Alg. 4) instead of the 3-path sampler,
+ * with their bars (C3 only the 3-path sampler sees).  flags bit 1: report
+ * Alg. 2's own estimates of C4..C6 (from the 3-path sampler) instead of the
+ * final combination's centred ones. */
 int or_estimate_ex(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
                    const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
-                   double delta, int c1_from_centred, double est[6], double lo[6], double hi[6]);
+                   double delta, int flags, double est[6], double lo[6], double hi[6]);
 
 int or_estimate(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
                 const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
@@ -498,8 +499,9 @@ int or_estimate(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
 
 int or_estimate_ex(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
                    const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4], uint64_t kc,
-                   double delta, int c1_from_centred, double est[6], double lo[6], double hi[6]) {
-    if (k3 == 0 || kc == 0 || !(delta > 0.0 && delta < 1.0)) return OR_ERR_ARG;
+                   double delta, int flags, double est[6], double lo[6], double hi[6]) {
+    if (k3 == 0 || kc == 0 || !(delta > 0.0 && delta < 1.0) || (flags & ~3)) return OR_ERR_ARG;
+    const int c1_from_centred = flags & 1, three_path_only = flags & 2;
     double n1 = (double)(((u128)n1_hi << 64) | (u128)n1_lo);
     double basic[7] = {0}, blo[7] = {0}, bhi[7] = {0};
     for (int i = 2; i <= 6; i++) {
@@ -537,9 +539,9 @@ int or_estimate_ex(uint64_t W, uint64_t Lambda, uint64_t n1_lo, uint64_t n1_hi,
         hi[i - 1] = bhi[i];
     }
     for (int i = 4; i <= 6; i++) {
-        est[i - 1] = cen[i];
-        lo[i - 1] = clo[i];
-        hi[i - 1] = chi[i];
+        est[i - 1] = three_path_only ? basic[i] : cen[i];
+        lo[i - 1] = three_path_only ? blo[i] : clo[i];
+        hi[i - 1] = three_path_only ? bhi[i] : chi[i];
     }
     return (W == 0 || Lambda == 0) ? OR_NO_PATHS : OR_OK;
 }

@@ -328,7 +328,7 @@ int ps_estimate_ex(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, con
                    uint64_t kc, double delta, uint32_t flags, double est[6], double lo[6], double hi[6]) {
     if (!st || !hist6 || !hist4 || !est || !lo || !hi) return PS_ERR_ARG;
     if (k3 == 0 || kc == 0 || !(delta > 0.0 && delta < 1.0)) return PS_ERR_ARG;
-    if (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED)) return PS_ERR_ARG;
+    if (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED | PS_EST_3PATH_ONLY)) return PS_ERR_ARG;
     // 3-paths per motif (row 2 of Eq. (1)) and centred 3-paths (Lemma 4.2)
     static const double kA2[7] = {0, 0, 1, 2, 4, 6, 12};
     static const double kB[7] = {0, 0, 0, 0, 1, 1, 3};
@@ -374,11 +374,13 @@ int ps_estimate_ex(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, con
         lo[i - 1] = clo[i];
         hi[i - 1] = chi[i];
     }
-    // the final combination (end of Section 4): C_4..C_6 from Alg. 4
+    // the final combination (end of Section 4): C_4..C_6 from Alg. 4, or on
+    // request Alg. 2's own estimates of them
+    const bool alg2 = (flags & PS_EST_3PATH_ONLY) != 0;
     for (int i = 4; i <= 6; i++) {
-        est[i - 1] = q[i];
-        lo[i - 1] = qlo[i];
-        hi[i - 1] = qhi[i];
+        est[i - 1] = alg2 ? c[i] : q[i];
+        lo[i - 1] = alg2 ? clo[i] : qlo[i];
+        hi[i - 1] = alg2 ? chi[i] : qhi[i];
     }
     return (st->W == 0 || st->Lambda == 0) ? PS_NO_PATHS : PS_OK;
 }
@@ -397,7 +399,9 @@ int ps_count_adaptive(const ps_graph *g, uint64_t seed, double target, double de
     if (!g || !d_hist6 || !d_hist4 || !k_used || !hist6 || !hist4 || !est || !lo || !hi) return PS_ERR_ARG;
     if (!g->prefixed) return PS_ERR_STATE;
     if (k0 == 0 || k_max < k0 || !(target > 0.0) || !(delta > 0.0 && delta < 1.0)) return PS_ERR_ARG;
-    if ((motif_mask & ~0x3fu) != 0 || (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED))) return PS_ERR_ARG;
+    if ((motif_mask & ~0x3fu) != 0 ||
+        (flags & ~static_cast<uint32_t>(PS_EST_C1_FROM_CENTRED | PS_EST_3PATH_ONLY)))
+        return PS_ERR_ARG;
     DeviceGuard dg(g->device);
     if (!dg.ok) return PS_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

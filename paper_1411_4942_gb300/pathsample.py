@@ -34,6 +34,7 @@ EXPORTED = [
 ]
 
 PS_EST_C1_FROM_CENTRED = 1
+PS_EST_3PATH_ONLY = 2
 
 
 class PathSampleError(RuntimeError):

@@ -29,7 +29,7 @@ def test_estimate_options_match_oracle(c1_from_centred):
         assert rc == ost
         for a, b in ((est, oest), (lo, olo), (hi, ohi)):
             np.testing.assert_allclose(a, b, rtol=EST_RTOL)
-    assert ps.ps_estimate_ex(G.stats, h6, k, h4, k, 0.01, 2)[0] == ps.PS_ERR_ARG
+    assert ps.ps_estimate_ex(G.stats, h6, k, h4, k, 0.01, 4)[0] == ps.PS_ERR_ARG
 
 
 @pytest.mark.parametrize("case", [

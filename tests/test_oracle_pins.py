@@ -583,3 +583,19 @@ def test_csr_from_edges_matches_generator_and_validates():
         listed = {(min(a, b), max(a, b)) for a, b in zip(src.tolist(), dst.tolist()) if a != b}
         got = {(u, int(v)) for u in range(n) for v in col[off[u]:off[u + 1]] if u < v}
         assert listed == got
+
+
+def test_three_path_only_estimates():
+    # Alg. 2 estimates every motif with a 3-path: on exact outcome histograms
+    # its C4..C6 are exact too, and the flag leaves C1..C3 alone
+    for t in range(5):
+        g = gg.gnp(16, 0.5, 170 + t)
+        og = O.prepare(g.off, g.col)
+        C = O.bruteforce_counts(g.off, g.col)
+        c6, c4 = O.enumerate_3path(og), O.enumerate_centered(og)
+        _, a, _, _ = O.estimate(og.W, og.Lambda, og.N1, c6, og.W, c4, og.Lambda, three_path_only=True)
+        assert np.allclose(a, C, rtol=1e-12, atol=1e-9)
+    h6, h4 = O.sample_3paths(og, 5000, 1), O.sample_centered(og, 5000, 1)
+    _, a, _, _ = O.estimate(og.W, og.Lambda, og.N1, h6, 5000, h4, 5000)
+    _, b, _, _ = O.estimate(og.W, og.Lambda, og.N1, h6, 5000, h4, 5000, three_path_only=True)
+    assert np.array_equal(a[:3], b[:3])
