@@ -162,6 +162,18 @@ class Server:
         self.iterations = 0
         self.items_launched = 0
 
+    def warmup(self):
+        """Runs each device operation of an iteration once, untimed: the first
+        use of a torch operation in a process loads its kernels, which took
+        seconds on a fresh host and stalled the first requests behind it."""
+        import torch
+        self._zero_slots([0])
+        sel = torch.tensor([0], dtype=torch.int64, device=self.pool.device)
+        self.d_hist.view(self.max_active, 12).index_select(0, sel).cpu()
+        torch.from_numpy(np.zeros(16, dtype=np.uint8)).pin_memory().to(self.pool.device, non_blocking=True)
+        torch.cuda.Event().record(self.streams[0])
+        torch.cuda.synchronize(self.pool.device)
+
     def _zero_slots(self, slots):
         """Clears reused histogram slots on the current stream; every launch
         stream waits on that stream before its kernel."""
@@ -192,6 +204,7 @@ class Server:
         False treats every request as arrived at the start (throughput).
         Returns (results, report); latencies are wall-clock seconds."""
         import torch
+        self.warmup()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
         active: dict = {}
