@@ -54,9 +54,10 @@ typedef struct {
     int32_t block_size;         /* sampling threads per block: 128, 256 (default), 512, 1024 */
     int32_t blocks_per_sm;      /* resident sampling blocks per SM (default: occupancy)      */
     int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1); -1 = none  */
-    int32_t hub_count;          /* top-degree vertices given an adjacency bitmap row (used by
-                                   adjacency 2; default there: up to 1024 rows within
-                                   256 MB, none with the hash set); -1 = none               */
+    int32_t hub_count;          /* top-degree vertices (degree >= 64) given an adjacency
+                                   bitmap row; default: up to 1024 rows within 256 MB
+                                   (adjacency 2) or 128 MB (adjacency 1, where a lookup
+                                   whose larger label is a hub reads its row); -1 = none   */
     int32_t samples_per_thread; /* reserved (1)                                             */
     int32_t adjacency;          /* adjacency test: 1 = hash set of the edges (default),
                                    2 = search of the sorted smaller list + hub bitmaps,

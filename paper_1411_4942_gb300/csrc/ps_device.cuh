@@ -395,6 +395,68 @@ __device__ __forceinline__ void eset_contains3(const uint64_t *set, uint64_t mas
     r2 = (x2 != y2) && (v2 >= 0 ? v2 == 1 : probe_on(set, mask, k2, b2));
 }
 
+// Hash set plus hub rows: a pair whose larger label is one of the top-degree
+// labels (>= hub_start, rows of the hub bitmap) is answered from that
+// hub's bitmap row, the rest from the hash set.  The sampled edges are
+// drawn in proportion to tau, so a lookup (u', v) mostly names a hub v: a
+// few dozen MB of hub rows then serve a large share of the lookups, and
+// their loads ask L2 to keep those lines (evict-last) while the hash set's
+// random buckets stream past.  With no hub rows (hub_start == n) this is the
+// plain hash-set test.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint32_t ld_hub_word(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Address of the hub-row word holding bit a of hub c's row.
+__device__ __forceinline__ const uint32_t *hub_word_of(const GraphDev &g, int32_t a, int32_t c) {
+    return g.hub + static_cast<int64_t>(c - g.hub_start) * g.hub_words + (a >> 5);
+}
+
+// Three independent tests (x != y for each pair) with all first loads in
+// flight together.  Only the first pair may go to a hub row: it is the one
+// that names an endpoint of the drawn edge (most often a hub), and keeping
+// the other two on the hash set holds the register count of the plain test.
+__device__ __forceinline__ void pair_test3(const GraphDev &g, int32_t x0, int32_t y0, int32_t x1,
+                                           int32_t y1, int32_t x2, int32_t y2, bool &r0, bool &r1,
+                                           bool &r2) {
+    const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
+    if (c0 < g.hub_start) {
+        eset_contains3(g.eset, g.eset_mask, x0, y0, x1, y1, x2, y2, r0, r1, r2);
+        return;
+    }
+    const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+    eset_contains2(g.eset, g.eset_mask, x1, y1, x2, y2, r1, r2);
+    r0 = ((w >> (a0 & 31)) & 1u) != 0u;
+}
+
+__device__ __forceinline__ bool pair_test(const GraphDev &g, int32_t x, int32_t y) {
+    const int32_t a = min(x, y), c = max(x, y);
+    if (c >= g.hub_start)
+        return x != y && ((ld_hub_word(hub_word_of(g, a, c), l2_keep_policy()) >> (a & 31)) & 1u);
+    return eset_contains(g.eset, g.eset_mask, x, y);
+}
+
+// Two independent tests (x != y for each pair); the first pair may go to a
+// hub row, as above.
+__device__ __forceinline__ void pair_test2(const GraphDev &g, int32_t x0, int32_t y0, int32_t x1,
+                                           int32_t y1, bool &r0, bool &r1) {
+    const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
+    if (c0 < g.hub_start) {
+        eset_contains2(g.eset, g.eset_mask, x0, y0, x1, y1, r0, r1);
+        return;
+    }
+    const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+    r1 = eset_contains(g.eset, g.eset_mask, x1, y1);
+    r0 = ((w >> (a0 & 31)) & 1u) != 0u;
+}
+
 // ------------------------------------------------ per-vertex hash tables
 
 // Each adjacency list in its own open-addressing table (Theorem 3.5 assumes

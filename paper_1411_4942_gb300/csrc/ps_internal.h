@@ -16,6 +16,8 @@ namespace ps {
 constexpr int kTierA = 32;      // one warp, one key per lane
 constexpr int kTierB = 1024;    // one warp, up to 32 keys per lane in registers
 constexpr int kTierC = 4096;    // one block, registers + 16 KB shared; above: block radix sort
+// Arc-to-row index: the row holding every 2^kArcRowShift-th arc.
+constexpr int kArcRowShift = 8;
 // Hub rows are only worth a bitmap above this degree.
 constexpr int kHubMinDegree = 64;
 // Items per tile of every scan.
@@ -41,7 +43,7 @@ struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
     int64_t eset_buckets;  // 0 without the edge hash set
     int64_t vtab_slots;    // 0 without the per-vertex tables
-    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab;
+    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab, arcrow;
     size_t keys0, keys1, vals0, vals1, rcounts, scan_flag, scan_agg, scan_inc;
     size_t total;
 };
@@ -70,6 +72,7 @@ struct ps_graph {
     uint32_t *hub;
     uint64_t *eset;
     int32_t *vtab;
+    int32_t *arcrow;  // row of every kArcRowStep-th arc of the canonical CSR
     bool prefixed;
     ps_stats stats;
     ps::GraphDev dev;

@@ -169,6 +169,34 @@ struct StoreOffsets {
     }
 };
 
+// arcrow[q] = the row holding arc q << kArcRowShift (every such arc lies in
+// exactly one non-empty row); arcrow[Q] = n - 1 closes the last interval.
+// Kernels that give each thread a run of arcs find its row between two
+// entries instead of searching all n offsets.
+__global__ void k_arc_rows(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, int32_t *arcrow) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t q_end = (nnz + (1ll << kArcRowShift) - 1) >> kArcRowShift;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int64_t a = coff[r], b = coff[r + 1];
+        for (int64_t q = (a + (1ll << kArcRowShift) - 1) >> kArcRowShift; (q << kArcRowShift) < b; q++)
+            arcrow[q] = static_cast<int32_t>(r);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) arcrow[q_end] = static_cast<int32_t>(n > 0 ? n - 1 : 0);
+}
+
+// Row of arc i (the last row r with coff[r] <= i), searched between the
+// arc-to-row entries around i.
+__device__ __forceinline__ int64_t row_of_arc(const int64_t *coff, const int32_t *arcrow, int64_t i) {
+    const int64_t q = i >> kArcRowShift;
+    int64_t lo = ldg_i32(arcrow + q), hi = ldg_i32(arcrow + q + 1);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (ldg_i64(coff + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // first row whose degree exceeds each tier limit (rows are degree-sorted)
 __global__ void k_tiers(int64_t n, const int32_t *__restrict__ dnew, u64 *status) {
     const int lim[4] = {0, kTierA, kTierB, kTierC};
@@ -687,19 +715,13 @@ __device__ __forceinline__ bool eset_insert(uint64_t *set, uint64_t mask, uint64
 // registers, both measured slower.)
 __global__ void __launch_bounds__(256)
 k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
-        const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, EdgeRec *rec,
-        int64_t m_cap, u64 *status) {
+        const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase,
+        const int32_t *__restrict__ arcrow, EdgeRec *rec, int64_t m_cap, u64 *status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     bool asym = false;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c * kEdgeItems < nnz; c += stride) {
         const int64_t i0 = c * kEdgeItems;
-        int64_t lo = 0, hi = n;  // last row r with coff[r] <= i0
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (ldg_i64(coff + mid) <= i0) lo = mid;
-            else hi = mid - 1;
-        }
-        int64_t r = lo;
+        int64_t r = row_of_arc(coff, arcrow, i0);
         int64_t ro = ldg_i64(coff + r);
         int64_t rend = ldg_i64(coff + r + 1);
         for (int t = 0; t < kEdgeItems; t++) {
@@ -862,6 +884,10 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     PS_CUDA_TRY(cudaMemsetAsync(g->off, 0, sizeof(int64_t), s));
     int rc = run_scan<int64_t>(g, 1, n, (int64_t)0, OpSum(), LoadDeg{g->dnew}, StoreOffsets{g->off, n}, s);
     if (rc) return rc;
+    if (n > 0) {
+        k_arc_rows<<<sms * 4, 256, 0, s>>>(n, nnz, g->off, g->arcrow);
+        PS_LAUNCH_CHECK();
+    }
     k_tiers<<<1, 32, 0, s>>>(n, g->dnew, g->status);
     PS_LAUNCH_CHECK();
 
@@ -911,8 +937,8 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     if (nnz > 0) {
         int64_t blocks = ((nnz + kEdgeItems - 1) / kEdgeItems + 255) / 256;
         if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
-        k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->rec,
-                                                 L.m_cap, g->status);
+        k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->arcrow,
+                                                 g->rec, L.m_cap, g->status);
         PS_LAUNCH_CHECK();
     }
 

@@ -109,20 +109,31 @@ k_guide_fill(int64_t m, const uint64_t *__restrict__ P, int shift, int32_t *G, i
     }
 }
 
-// One warp per hub row: set bit x of row h for every neighbour x.
-__global__ void __launch_bounds__(256)
-k_hub_bits(int64_t hub_start, int64_t n, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
-           uint32_t *bits, int64_t words) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t r = hub_start + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < n; r += nw) {
-        uint32_t *row = bits + (r - hub_start) * words;
-        const int64_t o = coff[r], e = coff[r + 1];
-        for (int64_t i = o + lane; i < e; i += 32) {
-            const int32_t x = ccol[i];
-            atomicOr(row + (x >> 5), 1u << (x & 31));
-        }
+// Hub bitmap rows, one block per (hub, chunk of 2^20 labels): the block sets
+// bit x for every neighbour x inside its chunk in shared memory, then writes
+// the chunk out whole (coalesced), so no clearing pass and no global atomics.
+constexpr int kHubThreads = 1024;
+constexpr int64_t kHubChunkWords = 1 << 15;  // 128 KB of shared memory
+
+__global__ void __launch_bounds__(kHubThreads)
+k_hub_rows(int64_t hub_start, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+           uint32_t *bits, int64_t words, int64_t chunks) {
+    extern __shared__ uint32_t s_row[];
+    const int64_t h = blockIdx.x / chunks, c = blockIdx.x % chunks;
+    const int64_t w0 = c * kHubChunkWords;
+    const int64_t nw = min(kHubChunkWords, words - w0);
+    for (int64_t w = threadIdx.x; w < nw; w += kHubThreads) s_row[w] = 0u;
+    __syncthreads();
+    const int64_t r = hub_start + h;
+    const int64_t o = coff[r], e = coff[r + 1];
+    const int64_t lo = w0 * 32, hi = (w0 + nw) * 32;
+    for (int64_t i = o + threadIdx.x; i < e; i += kHubThreads) {
+        const int64_t x = ccol[i];
+        if (x >= lo && x < hi) atomicOr(s_row + ((x - lo) >> 5), 1u << (x & 31));
     }
+    __syncthreads();
+    uint32_t *row = bits + h * words + w0;
+    for (int64_t w = threadIdx.x; w < nw; w += kHubThreads) row[w] = s_row[w];
 }
 
 // Inserts every arc (x -> y) into the table of x with compare-and-swap; the
@@ -256,10 +267,12 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     const int64_t hubs = static_cast<int64_t>(st[ST_HUBS]);
     S.hubs = hubs;
     if (hubs > 0) {
-        PS_CUDA_TRY(cudaMemsetAsync(g->hub, 0, sizeof(uint32_t) * hubs * g->L.hub_words, s));
-        int64_t blocks = (hubs * 32 + 255) / 256;
-        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
-        k_hub_bits<<<(unsigned)blocks, 256, 0, s>>>(n - hubs, n, g->off, g->col, g->hub, g->L.hub_words);
+        const int64_t words = g->L.hub_words;
+        const int64_t chunks = (words + kHubChunkWords - 1) / kHubChunkWords;
+        const int smem = static_cast<int>((words < kHubChunkWords ? words : kHubChunkWords) * sizeof(uint32_t));
+        PS_CUDA_TRY(cudaFuncSetAttribute(k_hub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_hub_rows<<<(unsigned)(hubs * chunks), kHubThreads, smem, s>>>(n - hubs, g->off, g->col, g->hub, words,
+                                                                        chunks);
         PS_LAUNCH_CHECK();
     }
     // The kernels queued after the synchronisation, and the hash set build,

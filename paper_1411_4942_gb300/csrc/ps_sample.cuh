@@ -33,7 +33,7 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
     bool e1, e2, e3;
     if (ADJ == kAdjHash) {
-        eset_contains3(g.eset, g.eset_mask, up, e.v, e.u, vp, up, vp, e1, e2, e3);
+        pair_test3(g, up, e.v, e.u, vp, up, vp, e1, e2, e3);
     } else if (ADJ == kAdjVtab) {
         // (u', v) in the table of v, (u, v') in the table of u -- both rows
         // are in the edge record -- and (u', v') in the larger label's table
@@ -94,9 +94,9 @@ __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, 
     }
     if (ADJ == kAdjHash) {
         // the closing edge first; the two chords only for centred paths
-        if (!eset_contains(g.eset, g.eset_mask, up, vp)) return 0;  // also u' == v'
+        if (!pair_test(g, up, vp)) return 0;  // also u' == v'
         bool c1, c2;
-        eset_contains2(g.eset, g.eset_mask, e.v, up, e.u, vp, c1, c2);
+        pair_test2(g, e.v, up, e.u, vp, c1, c2);
         return 1 + (int)c1 + (int)c2;
     }
     if (!adjacent(g, up, vp)) return 0;  // also covers u' == v'
