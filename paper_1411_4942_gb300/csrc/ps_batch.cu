@@ -33,7 +33,7 @@ static int table_adjacency(const void *d_table) {
 
 template <int ADJ>
 __device__ __forceinline__ int batch_sample(const GraphDev &g, int sampler, uint64_t seed, uint64_t id) {
-    return sampler == 0 ? sample_3path<ADJ>(g, seed, id) : sample_centred<ADJ>(g, seed, id);
+    return sampler == 0 ? sample_3path<ADJ, false>(g, seed, id) : sample_centred<ADJ, false>(g, seed, id);
 }
 
 // ADJ = 0: any variant, chosen per item; otherwise the table's only variant.

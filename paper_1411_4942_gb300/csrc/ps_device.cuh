@@ -419,21 +419,55 @@ __device__ __forceinline__ const uint32_t *hub_word_of(const GraphDev &g, int32_
     return g.hub + static_cast<int64_t>(c - g.hub_start) * g.hub_words + (a >> 5);
 }
 
+// One pair's first load: its hub-row word (in the first slot of the
+// returned bucket) when its larger label is a hub, else its home bucket.
+__device__ __forceinline__ Bucket load_pair(const GraphDev &g, int32_t a, int32_t c, uint64_t b) {
+    Bucket q;
+    if (c >= g.hub_start) {
+        q.q[0].x = ld_hub_word(hub_word_of(g, a, c), l2_keep_policy());
+    } else {
+        q = load_bucket(g.eset, b);
+    }
+    return q;
+}
+
+__device__ __forceinline__ bool resolve_pair(const GraphDev &g, int32_t a, int32_t c, uint64_t key,
+                                             uint64_t b, const Bucket &q) {
+    if (c >= g.hub_start) return ((q.q[0].x >> (a & 31)) & 1u) != 0u;
+    const int v = bucket_verdict(q, key);
+    return v >= 0 ? v == 1 : probe_on(g.eset, g.eset_mask, key, b);
+}
+
 // Three independent tests (x != y for each pair) with all first loads in
-// flight together.  Only the first pair may go to a hub row: it is the one
-// that names an endpoint of the drawn edge (most often a hub), and keeping
-// the other two on the hash set holds the register count of the plain test.
+// flight together; a pair whose larger label is a hub reads the hub's row.
+// ALL = false sends only the first pair to a hub row (it names an endpoint
+// of the drawn edge, most often a hub) and keeps the other two on the hash
+// set: fewer registers, for kernels that cannot spare them (the batched
+// kernel runs at 64).
+template <bool ALL>
 __device__ __forceinline__ void pair_test3(const GraphDev &g, int32_t x0, int32_t y0, int32_t x1,
                                            int32_t y1, int32_t x2, int32_t y2, bool &r0, bool &r1,
                                            bool &r2) {
     const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
-    if (c0 < g.hub_start) {
-        eset_contains3(g.eset, g.eset_mask, x0, y0, x1, y1, x2, y2, r0, r1, r2);
+    if (!ALL) {
+        if (c0 < g.hub_start) {
+            eset_contains3(g.eset, g.eset_mask, x0, y0, x1, y1, x2, y2, r0, r1, r2);
+            return;
+        }
+        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+        eset_contains2(g.eset, g.eset_mask, x1, y1, x2, y2, r1, r2);
+        r0 = ((w >> (a0 & 31)) & 1u) != 0u;
         return;
     }
-    const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
-    eset_contains2(g.eset, g.eset_mask, x1, y1, x2, y2, r1, r2);
-    r0 = ((w >> (a0 & 31)) & 1u) != 0u;
+    const int32_t a1 = min(x1, y1), c1 = max(x1, y1);
+    const int32_t a2 = min(x2, y2), c2 = max(x2, y2);
+    const uint64_t k0 = edge_key(a0, c0), k1 = edge_key(a1, c1), k2 = edge_key(a2, c2);
+    const uint64_t b0 = key_bucket(k0, g.eset_mask), b1 = key_bucket(k1, g.eset_mask),
+                   b2 = key_bucket(k2, g.eset_mask);
+    const Bucket q0 = load_pair(g, a0, c0, b0), q1 = load_pair(g, a1, c1, b1), q2 = load_pair(g, a2, c2, b2);
+    r0 = resolve_pair(g, a0, c0, k0, b0, q0);
+    r1 = resolve_pair(g, a1, c1, k1, b1, q1);
+    r2 = resolve_pair(g, a2, c2, k2, b2, q2);
 }
 
 __device__ __forceinline__ bool pair_test(const GraphDev &g, int32_t x, int32_t y) {
@@ -443,18 +477,28 @@ __device__ __forceinline__ bool pair_test(const GraphDev &g, int32_t x, int32_t 
     return eset_contains(g.eset, g.eset_mask, x, y);
 }
 
-// Two independent tests (x != y for each pair); the first pair may go to a
-// hub row, as above.
+// Two independent tests (x != y for each pair), both loads in flight; ALL as
+// for pair_test3.
+template <bool ALL>
 __device__ __forceinline__ void pair_test2(const GraphDev &g, int32_t x0, int32_t y0, int32_t x1,
                                            int32_t y1, bool &r0, bool &r1) {
     const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
-    if (c0 < g.hub_start) {
-        eset_contains2(g.eset, g.eset_mask, x0, y0, x1, y1, r0, r1);
+    if (!ALL) {
+        if (c0 < g.hub_start) {
+            eset_contains2(g.eset, g.eset_mask, x0, y0, x1, y1, r0, r1);
+            return;
+        }
+        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+        r1 = eset_contains(g.eset, g.eset_mask, x1, y1);
+        r0 = ((w >> (a0 & 31)) & 1u) != 0u;
         return;
     }
-    const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
-    r1 = eset_contains(g.eset, g.eset_mask, x1, y1);
-    r0 = ((w >> (a0 & 31)) & 1u) != 0u;
+    const int32_t a1 = min(x1, y1), c1 = max(x1, y1);
+    const uint64_t k0 = edge_key(a0, c0), k1 = edge_key(a1, c1);
+    const uint64_t b0 = key_bucket(k0, g.eset_mask), b1 = key_bucket(k1, g.eset_mask);
+    const Bucket q0 = load_pair(g, a0, c0, b0), q1 = load_pair(g, a1, c1, b1);
+    r0 = resolve_pair(g, a0, c0, k0, b0, q0);
+    r1 = resolve_pair(g, a1, c1, k1, b1, q1);
 }
 
 // ------------------------------------------------ per-vertex hash tables

@@ -13,7 +13,9 @@ namespace ps {
 
 // Class of one Alg. 1 output: 0 = triangle (u' == v'), 1 = 3-path,
 // 2 = tailed triangle, 3 = 4-cycle, 4 = chordal 4-cycle, 5 = 4-clique.
-template <int ADJ>
+// HUB_ALL: every adjacency test of a sample may read a hub row (see
+// pair_test3); false for kernels short of registers.
+template <int ADJ, bool HUB_ALL = true>
 __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, uint64_t id) {
     const uint4 w = sample_block(seed, id, 0, 0);
     uint64_t r;
@@ -33,7 +35,7 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
     bool e1, e2, e3;
     if (ADJ == kAdjHash) {
-        pair_test3(g, up, e.v, e.u, vp, up, vp, e1, e2, e3);
+        pair_test3<HUB_ALL>(g, up, e.v, e.u, vp, up, vp, e1, e2, e3);
     } else if (ADJ == kAdjVtab) {
         // (u', v) in the table of v, (u, v') in the table of u -- both rows
         // are in the edge record -- and (u', v') in the larger label's table
@@ -61,7 +63,7 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
 // 4-cycle, 3 = 4-clique.  u' is drawn among the L_{u,v} entries of N(u)
 // after v, v' among the L_{v,u} entries of N(v) after u; the path is centred
 // (Definition 4.1) iff (u', v') is an edge.
-template <int ADJ>
+template <int ADJ, bool HUB_ALL = true>
 __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, uint64_t id) {
     const uint4 w = sample_block(seed, id, 0, 1);
     uint64_t r;
@@ -96,7 +98,7 @@ __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, 
         // the closing edge first; the two chords only for centred paths
         if (!pair_test(g, up, vp)) return 0;  // also u' == v'
         bool c1, c2;
-        pair_test2(g, e.v, up, e.u, vp, c1, c2);
+        pair_test2<HUB_ALL>(g, e.v, up, e.u, vp, c1, c2);
         return 1 + (int)c1 + (int)c2;
     }
     if (!adjacent(g, up, vp)) return 0;  // also covers u' == v'
