@@ -131,8 +131,8 @@ __device__ __forceinline__ uint64_t ldg_u64(const uint64_t *p) {
 #endif
 }
 // Gathers of the skewed "hot" structures (guide entries, prefix probes).
-// (Evict-last L2 hints on these and evict-first on the hash buckets were
-// measured: no gain.)
+// (Evict-last L2 hints on these, on the hub rows' adjacency lists, and
+// evict-first on the hash buckets were measured: no gain.)
 __device__ __forceinline__ int32_t ldg_i32_hot(const int32_t *p) { return ldg_i32(p); }
 __device__ __forceinline__ uint64_t ldg_u64_hot(const uint64_t *p) { return ldg_u64(p); }
 
