@@ -4,8 +4,10 @@
 One step = the whole path over one synthetic graph resident in HBM:
 validation + degree-order relabel + sorted rows + edge table (ps_load_csr),
 tau / lambda prefixes + guide tables + hub bitmaps (ps_tau_prefix), k3
-samples of Alg. 1 and kc samples of Alg. 3 (ps_sample_3paths /
-ps_sample_centered), the histograms read back and the estimates with error
+samples of Alg. 1 and kc samples of Alg. 3 taken in edge-draw order
+(ps_sample_3paths_ordered / ps_sample_centered_ordered: the same counts as
+ps_sample_3paths / ps_sample_centered), the histograms read back and the
+estimates with error
 bars (ps_estimate).  value = (k3 + kc) samples per second of step time, timed
 with CUDA events on the launching stream, L2 flushed between steps.
 
@@ -39,6 +41,8 @@ SECTOR = 32
 # one 32-byte sector per random access): 3-path = edge draw, edge record,
 # both endpoint offsets, the two neighbour reads and three adjacency lookups
 BYTES_3PATH = 9 * SECTOR
+# samples per chunk of the draw-ordered samplers
+ORDER_CHUNK = 1 << 24
 
 
 def workloads():
@@ -237,6 +241,9 @@ def run_cuda(args):
         nb = ps.ps_graph_workspace_bytes(g.n, g.nnz)
         ws = torch.empty(nb, dtype=torch.uint8, device=device)
         hist = torch.zeros(16, dtype=torch.int64, device=device)
+        # scratch of the draw-ordered samplers: one chunk of max(k3, kc) samples
+        osb = ps.ps_ordered_scratch_bytes(min(max(k3, kc, 1), ORDER_CHUNK))
+        oscr = torch.empty(osb, dtype=torch.uint8, device=device)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
               for _ in range(args.steps + args.warmup)]
@@ -252,11 +259,13 @@ def run_cuda(args):
             ps._check(rc, "ps_tau_prefix", (ps.PS_OK, ps.PS_NO_PATHS))
             e[1].record(stream)
             hist.zero_()
-            ps._check(ps.ps_sample_3paths(h, k3, seed, first3, hist.data_ptr(), sp),
-                      "ps_sample_3paths", (ps.PS_OK, ps.PS_NO_PATHS))
+            ps._check(ps.ps_sample_3paths_ordered(h, k3, seed, first3, hist.data_ptr(),
+                                                  oscr.data_ptr(), osb, sp),
+                      "ps_sample_3paths_ordered", (ps.PS_OK, ps.PS_NO_PATHS))
             e[2].record(stream)
-            ps._check(ps.ps_sample_centered(h, kc, seed, firstc, hist.data_ptr() + 64, sp),
-                      "ps_sample_centered", (ps.PS_OK, ps.PS_NO_PATHS))
+            ps._check(ps.ps_sample_centered_ordered(h, kc, seed, firstc, hist.data_ptr() + 64,
+                                                    oscr.data_ptr(), osb, sp),
+                      "ps_sample_centered_ordered", (ps.PS_OK, ps.PS_NO_PATHS))
             e[3].record(stream)
             hh = hist.cpu().numpy().astype(np.uint64)
             rc, est, lo, hi = ps.ps_estimate(st, hh[:6], k3, hh[8:12], kc, 0.01)
@@ -307,7 +316,7 @@ def run_cuda(args):
     if not args.no_e2e:
         h_off = torch.as_tensor(g.off).pin_memory()
         h_col = torch.as_tensor(g.col).pin_memory()
-        nb2 = ps.ps_end_to_end_workspace_bytes(g.n, g.nnz)
+        nb2 = ps.ps_end_to_end_workspace_bytes(g.n, g.nnz) + osb  # + draw-order scratch
         del ws
         ws2 = torch.empty(nb2, dtype=torch.uint8, device=device)
         times = []
@@ -350,7 +359,9 @@ def run_cuda(args):
                              "readback_and_estimate": statistics.mean(est_ms)},
             "kernel_rates": {"3path_samples_per_s": k3 / (avg3 / 1e3),
                              "centred_samples_per_s": kc / (avgc / 1e3)},
-            "roofline": {"bound": "hbm", "kernel": "k_sample<3-path>", "achieved": achieved,
+            "roofline": {"bound": "hbm",
+                         "kernel": "3-path sampler call: draw sort + k_sample_ordered<3-path>",
+                         "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_source": peak_kind,
                          "bytes_per_sample": BYTES_3PATH},

@@ -62,7 +62,11 @@ typedef struct {
     int32_t adjacency;          /* adjacency test: 1 = hash set of the edges (default),
                                    2 = search of the sorted smaller list + hub bitmaps,
                                    3 = a hash table per adjacency list                      */
-    int32_t reserved[2];
+    int32_t draw_order;         /* the *_ordered samplers: 0 (default) sort each chunk of
+                                   samples by edge draw when the graph has >= 2^20 edges
+                                   and the chunk >= 2^18 samples, else take them in id
+                                   order; 1 = always sort; -1 = never                       */
+    int32_t reserved;
 } ps_tuning;
 
 /* Totals of one graph, filled by ps_tau_prefix. */
@@ -136,6 +140,29 @@ int ps_sample_3paths(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
  * Asynchronous.  Returns PS_NO_PATHS (adds nothing) when Lambda == 0. */
 int ps_sample_centered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
                        uint64_t *d_hist4, ps_stream_t stream);
+
+/* The same two samplers with the samples taken in the order of their edge
+ * draws.  The samples of Alg. 1 and Alg. 3 are independent and the
+ * histograms are sums, so the counts are exactly those of
+ * ps_sample_3paths / ps_sample_centered for the same (k, seed, first_id);
+ * only the memory traffic changes: the ids of each chunk are first sorted by
+ * their draw r (equal-width ranges of [0, W) or [0, Lambda)), so samples in
+ * flight together read neighbouring edge records and rows.
+ *
+ * d_scratch: caller-owned device memory, 16-byte aligned, of
+ * ps_ordered_scratch_bytes(k_chunk) bytes for chunks of k_chunk samples
+ * (1 <= k_chunk <= 2^31; larger k runs in several chunks).  It is the
+ * call's own working memory until the work queued on `stream` has run, so
+ * concurrent calls need separate scratch.  Asynchronous.  Returns
+ * PS_ERR_WORKSPACE when the scratch is missing, misaligned or smaller than
+ * ps_ordered_scratch_bytes(1); otherwise as the plain samplers. */
+size_t ps_ordered_scratch_bytes(uint64_t k_chunk);
+int ps_sample_3paths_ordered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
+                             uint64_t *d_hist6, void *d_scratch, size_t scratch_bytes,
+                             ps_stream_t stream);
+int ps_sample_centered_ordered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id,
+                               uint64_t *d_hist4, void *d_scratch, size_t scratch_bytes,
+                               ps_stream_t stream);
 
 /* The estimators of Alg. 2 and Alg. 4 and the final combination of
  * Section 4 (C1..C3 from the 3-path counts, C4..C6 from the centred counts;
@@ -223,7 +250,10 @@ int ps_graph_copy(const ps_graph *g, int which, void *dst, size_t bytes, ps_stre
  * and kc centred samples (seed, ids from 0), copies the histograms back and
  * fills est / lo / hi as ps_estimate.  hist6 / hist4 (host, may be NULL)
  * receive the class counts.  d_workspace must hold
- * ps_end_to_end_workspace_bytes(n, nnz, t) bytes.  Synchronises `stream`. */
+ * ps_end_to_end_workspace_bytes(n, nnz, t) bytes; when it holds at least
+ * ps_ordered_scratch_bytes(1) more, the rest is the scratch of the
+ * draw-ordered samplers, which then take the samples (same counts).
+ * Synchronises `stream`. */
 size_t ps_end_to_end_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
 int ps_count_motifs_host(int64_t n, int64_t nnz, const int64_t *h_off, const int32_t *h_col,
                          uint64_t k3, uint64_t kc, uint64_t seed, double delta,

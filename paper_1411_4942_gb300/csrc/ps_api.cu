@@ -80,6 +80,7 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
     r.guide_log2_ratio = 1;
     r.samples_per_thread = 1;
     r.adj_mode = kAdjHash;
+    r.draw_order = 0;
     if (t && (t->adjacency == kAdjSearch || t->adjacency == kAdjVtab)) r.adj_mode = t->adjacency;
     // hub bitmap rows: up to 1024 within 256 MB for the search variant, which
     // needs them for every hub pair; up to 1024 within 128 MB beside the hash
@@ -99,6 +100,7 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
         if (t->hub_count < 0) r.hub_count = 0;
         else if (t->hub_count > 0) r.hub_count = t->hub_count;
         if (t->samples_per_thread > 0) r.samples_per_thread = t->samples_per_thread;
+        r.draw_order = t->draw_order > 0 ? 1 : (t->draw_order < 0 ? -1 : 0);
     }
     if (r.hub_count > n) r.hub_count = static_cast<int>(n);
     return r;
@@ -325,6 +327,34 @@ int ps_sample_centered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t fi
     return sample_common(g, 1, k, seed, first_id, d_hist4, stream);
 }
 
+size_t ps_ordered_scratch_bytes(uint64_t k_chunk) { return ordered_scratch_bytes(k_chunk); }
+
+static int ordered_common(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id,
+                          uint64_t *d_hist, void *d_scratch, size_t scratch_bytes, ps_stream_t stream) {
+    if (!g || !d_hist) return PS_ERR_ARG;
+    if (!g->prefixed) return PS_ERR_STATE;
+    if (!d_scratch || (reinterpret_cast<uintptr_t>(d_scratch) & 15u) != 0 ||
+        scratch_bytes < ordered_scratch_bytes(1))
+        return PS_ERR_WORKSPACE;
+    const uint64_t total = sampler == 0 ? g->stats.W : g->stats.Lambda;
+    if (total == 0) return PS_NO_PATHS;
+    if (k == 0) return PS_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PS_ERR_CUDA;
+    return launch_ordered(g, sampler, k, seed, first_id, d_hist, d_scratch, scratch_bytes,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ps_sample_3paths_ordered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *d_hist6,
+                             void *d_scratch, size_t scratch_bytes, ps_stream_t stream) {
+    return ordered_common(g, 0, k, seed, first_id, d_hist6, d_scratch, scratch_bytes, stream);
+}
+
+int ps_sample_centered_ordered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *d_hist4,
+                               void *d_scratch, size_t scratch_bytes, ps_stream_t stream) {
+    return ordered_common(g, 1, k, seed, first_id, d_hist4, d_scratch, scratch_bytes, stream);
+}
+
 int ps_estimate(const ps_stats *st, const uint64_t hist6[6], uint64_t k3, const uint64_t hist4[4],
                 uint64_t kc, double delta, double est[6], double lo[6], double hi[6]) {
     return ps_estimate_ex(st, hist6, k3, hist4, kc, delta, 0u, est, lo, hi);
@@ -529,8 +559,17 @@ int ps_count_motifs_host(int64_t n, int64_t nnz, const int64_t *h_off, const int
         ps_graph_free(g);
         return rc;
     }
-    if (st.W > 0) rc = ps_sample_3paths(g, k3, seed, 0, d_hist, stream);
-    if (rc >= 0 && st.Lambda > 0) rc = ps_sample_centered(g, kc, seed, 0, d_hist + 8, stream);
+    // bytes beyond the minimum: scratch of the draw-ordered samplers
+    const size_t used = gbytes + e2e_extra(n, nnz);
+    void *oscr = static_cast<char *>(d_workspace) + used;
+    const size_t obytes = ws_bytes - used;
+    const bool ordered = obytes >= ordered_scratch_bytes(1);
+    if (st.W > 0)
+        rc = ordered ? ps_sample_3paths_ordered(g, k3, seed, 0, d_hist, oscr, obytes, stream)
+                     : ps_sample_3paths(g, k3, seed, 0, d_hist, stream);
+    if (rc >= 0 && st.Lambda > 0)
+        rc = ordered ? ps_sample_centered_ordered(g, kc, seed, 0, d_hist + 8, oscr, obytes, stream)
+                     : ps_sample_centered(g, kc, seed, 0, d_hist + 8, stream);
     if (rc < 0) {
         ps_graph_free(g);
         return rc;

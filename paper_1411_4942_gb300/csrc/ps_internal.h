@@ -36,6 +36,7 @@ struct Tuning {
     int hub_count;         // 0: none
     int samples_per_thread;
     int adj_mode;          // kAdjHash or kAdjSearch
+    int draw_order;        // ordered samplers: 0 by size, 1 always, -1 never
 };
 Tuning resolve_tuning(const ps_tuning *t, int64_t n);
 
@@ -142,6 +143,12 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
 int prefix_graph(ps_graph *g, cudaStream_t s);
 int launch_sampler(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id,
                    uint64_t *d_hist, cudaStream_t s);
+// Samples in the order of their edge draws (ps_order.cu); ids of a chunk are
+// 32-bit offsets, so a chunk holds at most kOrderMaxChunk samples.
+constexpr uint64_t kOrderMaxChunk = 1ull << 31;
+size_t ordered_scratch_bytes(uint64_t k_chunk);
+int launch_ordered(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *d_hist,
+                   void *d_scratch, size_t scratch_bytes, cudaStream_t s);
 int launch_batch(const void *d_table, int32_t n_graphs, const ps_work *d_items, int64_t n_items,
                  uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s);
 // Records the adjacency variant shared by a descriptor table's graphs (0: mixed).

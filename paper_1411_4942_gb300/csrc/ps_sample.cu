@@ -6,13 +6,6 @@
 
 namespace ps {
 
-// Registers for 768 resident threads per SM (three blocks of 256, 85
-// registers): the hub-row tests otherwise take 98 and drop to two blocks
-// (3-path sampling on R-MAT 20: 1.61 ms capped, 1.74 ms not).  Blocks of 512
-// and 1024 keep the compiler's choice.
-template <int BLOCK>
-constexpr int sample_min_blocks() { return BLOCK <= 256 ? 768 / BLOCK : 1; }
-
 template <int SAMPLER, int BLOCK, int ADJ>
 __global__ void __launch_bounds__(BLOCK, sample_min_blocks<BLOCK>())
 k_sample(GraphDev g, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *hist) {

@@ -108,6 +108,13 @@ __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, 
     return 1 + (int)c1 + (int)c2;
 }
 
+// Registers for 768 resident threads per SM (three blocks of 256, 85
+// registers): the hub-row tests otherwise take 98 and drop to two blocks
+// (3-path sampling on R-MAT 20: 1.61 ms capped, 1.74 ms not).  Blocks of 512
+// and 1024 keep the compiler's choice.
+template <int BLOCK>
+constexpr int sample_min_blocks() { return BLOCK <= 256 ? 768 / BLOCK : 1; }
+
 // Per-thread class counters kept in registers.
 struct Counts6 {
     uint32_t c[6];

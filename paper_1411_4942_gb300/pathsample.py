@@ -30,7 +30,8 @@ EXPORTED = [
     "ps_end_to_end_workspace_bytes", "ps_count_motifs_host", "ps_batch_table_bytes",
     "ps_batch_sample", "ps_batch_prepare", "ps_batch_sample_prepared", "ps_kernel_launches",
     "ps_exact_scratch_bytes", "ps_count_exact", "ps_estimate_ex", "ps_count_adaptive",
-    "ps_ingest_workspace_bytes", "ps_csr_from_edges",
+    "ps_ingest_workspace_bytes", "ps_csr_from_edges", "ps_ordered_scratch_bytes",
+    "ps_sample_3paths_ordered", "ps_sample_centered_ordered",
 ]
 
 PS_EST_C1_FROM_CENTRED = 1
@@ -47,7 +48,7 @@ class PsTuning(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("guide_log2_ratio", ctypes.c_int32), ("hub_count", ctypes.c_int32),
                 ("samples_per_thread", ctypes.c_int32), ("adjacency", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("draw_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PsStats(ctypes.Structure):
@@ -104,6 +105,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_tau_prefix": ([V, V, P(PsStats)], I32),
             "ps_sample_3paths": ([V, U64, U64, U64, V, V], I32),
             "ps_sample_centered": ([V, U64, U64, U64, V, V], I32),
+            "ps_ordered_scratch_bytes": ([U64], SZ),
+            "ps_sample_3paths_ordered": ([V, U64, U64, U64, V, V, SZ, V], I32),
+            "ps_sample_centered_ordered": ([V, U64, U64, U64, V, V, SZ, V], I32),
             "ps_estimate": ([P(PsStats), V, U64, V, U64, ctypes.c_double, V, V, V], I32),
             "ps_graph_free": ([V], None),
             "ps_strerror": ([I32], ctypes.c_char_p),
@@ -189,6 +193,23 @@ def ps_sample_3paths(handle, k, seed, first_id, d_hist6, stream=None) -> int:
 def ps_sample_centered(handle, k, seed, first_id, d_hist4, stream=None) -> int:
     return int(load_library().ps_sample_centered(handle, k, seed, first_id, d_hist4,
                                                  _stream_ptr(stream)))
+
+
+def ps_ordered_scratch_bytes(k_chunk) -> int:
+    return int(load_library().ps_ordered_scratch_bytes(k_chunk))
+
+
+def ps_sample_3paths_ordered(handle, k, seed, first_id, d_hist6, d_scratch, scratch_bytes,
+                             stream=None) -> int:
+    return int(load_library().ps_sample_3paths_ordered(handle, k, seed, first_id, d_hist6, d_scratch,
+                                                       scratch_bytes, _stream_ptr(stream)))
+
+
+def ps_sample_centered_ordered(handle, k, seed, first_id, d_hist4, d_scratch, scratch_bytes,
+                               stream=None) -> int:
+    return int(load_library().ps_sample_centered_ordered(handle, k, seed, first_id, d_hist4,
+                                                         d_scratch, scratch_bytes,
+                                                         _stream_ptr(stream)))
 
 
 def ps_estimate(stats: PsStats, hist6, k3: int, hist4, kc: int, delta: float = 0.01):
@@ -345,11 +366,11 @@ ADJ_HASH, ADJ_SEARCH, ADJ_VTAB = 1, 2, 3
 
 
 def make_tuning(block_size=0, blocks_per_sm=0, guide_log2_ratio=0, hub_count=0,
-                adjacency=0) -> PsTuning:
+                adjacency=0, draw_order=0) -> PsTuning:
     t = PsTuning()
     t.block_size, t.blocks_per_sm = block_size, blocks_per_sm
     t.guide_log2_ratio, t.hub_count = guide_log2_ratio, hub_count
-    t.adjacency = adjacency
+    t.adjacency, t.draw_order = adjacency, draw_order
     return t
 
 
@@ -415,6 +436,36 @@ class Graph:
         hist = self.new_hist() if hist is None else hist
         rc = ps_sample_centered(self.handle, k, seed, first_id, hist.data_ptr(), stream)
         _check(rc, "ps_sample_centered", (PS_OK, PS_NO_PATHS))
+        return hist
+
+    ORDER_CHUNK = 1 << 24
+
+    def order_scratch(self, k: int):
+        """Scratch of the ordered samplers for chunks of min(k, 2^24) samples,
+        kept for the next calls (one scratch per Graph: calls on different
+        streams need their own, passed to the ps_* functions directly)."""
+        import torch
+        need = ps_ordered_scratch_bytes(max(1, min(int(k), self.ORDER_CHUNK)))
+        cur = getattr(self, "_order_scratch", None)
+        if cur is None or cur.numel() < need:
+            cur = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self._order_scratch = cur
+        return cur
+
+    def sample_3paths_ordered(self, k: int, seed: int, first_id: int = 0, hist=None, stream=None):
+        hist = self.new_hist() if hist is None else hist
+        sc = self.order_scratch(k)
+        rc = ps_sample_3paths_ordered(self.handle, k, seed, first_id, hist.data_ptr(), sc.data_ptr(),
+                                      sc.numel(), stream)
+        _check(rc, "ps_sample_3paths_ordered", (PS_OK, PS_NO_PATHS))
+        return hist
+
+    def sample_centered_ordered(self, k: int, seed: int, first_id: int = 0, hist=None, stream=None):
+        hist = self.new_hist() if hist is None else hist
+        sc = self.order_scratch(k)
+        rc = ps_sample_centered_ordered(self.handle, k, seed, first_id, hist.data_ptr(),
+                                        sc.data_ptr(), sc.numel(), stream)
+        _check(rc, "ps_sample_centered_ordered", (PS_OK, PS_NO_PATHS))
         return hist
 
     def copy(self, which: int) -> np.ndarray:

@@ -241,15 +241,20 @@ def test_end_to_end_host_call():
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     off = torch.as_tensor(g.off).pin_memory()
     col = torch.as_tensor(g.col).pin_memory()
-    rc, est, lo, hi, h6, h4, st = ps.ps_count_motifs_host(off, col, 200000, 150000, 17, 0.01,
-                                                          ws.data_ptr(), nb)
-    assert rc == ps.PS_OK
     r6 = O.sample_3paths(og, 200000, 17, threads=8)
     r4 = O.sample_centered(og, 150000, 17, threads=8)
-    assert h6.tolist() == r6.tolist() and h4.tolist() == r4.tolist()
     _, oest, olo, ohi = O.estimate(og.W, og.Lambda, og.N1, r6, 200000, r4, 150000, 0.01)
-    np.testing.assert_allclose(est, oest, rtol=EST_RTOL)
-    np.testing.assert_allclose(hi, ohi, rtol=EST_RTOL)
+    # the minimum workspace (samples in id order), then room for the
+    # draw-ordered samplers, forced on for this small graph
+    extra = ps.ps_ordered_scratch_bytes(200000)
+    big = torch.empty(nb + extra, dtype=torch.uint8, device="cuda")
+    for buf, size, tun in ((ws, nb, None), (big, nb + extra, ps.make_tuning(draw_order=1))):
+        rc, est, lo, hi, h6, h4, st = ps.ps_count_motifs_host(off, col, 200000, 150000, 17, 0.01,
+                                                              buf.data_ptr(), size, tun)
+        assert rc == ps.PS_OK
+        assert h6.tolist() == r6.tolist() and h4.tolist() == r4.tolist()
+        np.testing.assert_allclose(est, oest, rtol=EST_RTOL)
+        np.testing.assert_allclose(hi, ohi, rtol=EST_RTOL)
 
 
 def test_batched_launch_matches_plain_calls():
