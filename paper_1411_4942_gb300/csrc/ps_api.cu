@@ -189,9 +189,13 @@ static void binomial_bar(uint64_t count, uint64_t k, double delta, double *pl, d
         *pu = 1.0;
         return;
     }
+    // 200 halvings at most; once the midpoint rounds to an end the interval
+    // can only stay or shrink onto that point, so stopping there returns the
+    // same double as running on
     double a = 0.0, b = alpha;
     for (int i = 0; i < 200; i++) {
         const double mid = 0.5 * (a + b);
+        if (mid == a || mid == b) break;
         if (kl_div(alpha, mid) > target) a = mid;
         else b = mid;
     }
@@ -200,6 +204,7 @@ static void binomial_bar(uint64_t count, uint64_t k, double delta, double *pl, d
     b = 1.0;
     for (int i = 0; i < 200; i++) {
         const double mid = 0.5 * (a + b);
+        if (mid == a || mid == b) break;
         if (kl_div(alpha, mid) > target) b = mid;
         else a = mid;
     }

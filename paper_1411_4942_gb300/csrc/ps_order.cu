@@ -17,18 +17,22 @@
 
 namespace ps {
 
-// kOrderBuckets equal-width ranges of r; a chunk of ids is split into at most
-// kOrderMaxBlocks contiguous runs, one per block of the counting sort, which
-// keeps its bucket counters in shared memory.
-constexpr int kOrderBuckets = 1 << 14;
-constexpr int kOrderMaxBlocks = 512;
+// kOrderBuckets equal-width ranges of r; a chunk of ids is split into at
+// most kOrderMaxRuns contiguous runs, one per block of the counting sort.
+// On R-MAT 20 with 2^24 samples, finer orders made the 3-path sampling
+// kernel faster (1.08 ms at 256 buckets, 0.96 ms at 65536 through a second
+// pass, 0.94 ms with global atomics) but cost more to sort than they saved.
+constexpr int kOrderBuckets = 256;
+constexpr int kOrderMaxRuns = 1024;
 constexpr int kOrderThreads = 512;
-constexpr int kOrderSmem = kOrderBuckets * static_cast<int>(sizeof(uint32_t));
-constexpr size_t kOrderHist = static_cast<size_t>(kOrderMaxBlocks) * kOrderBuckets * sizeof(uint32_t);
-constexpr size_t kOrderHeader = kOrderHist + kOrderBuckets * sizeof(uint32_t);  // run counts, bases
-// after the header: the chunk's ids (uint32), then their buckets (uint16)
-constexpr int kOrderScanThreads = 1024;
-constexpr int kOrderPerThread = kOrderBuckets / kOrderScanThreads;
+constexpr int kOrderWarps = kOrderThreads / 32;
+constexpr int kOrderItems = 8;                            // ids per scatter thread and tile
+constexpr int kOrderTile = kOrderItems * kOrderThreads;   // ids a scatter block sorts in shared memory at once
+// hist[b * kOrderMaxRuns + run]: run counts, then offsets; then the bucket totals
+constexpr size_t kOrderHist = static_cast<size_t>(kOrderMaxRuns) * kOrderBuckets * sizeof(uint32_t);
+constexpr size_t kOrderHeader = kOrderHist + kOrderBuckets * sizeof(uint32_t);
+// after the header, per sample of a chunk: its bucket (uint8) and its
+// position in the sorted order (uint32 id offset)
 // By default (tuning draw_order 0) chunks below kOrderMinChunk samples, and
 // graphs below kOrderMinEdges edges (whose records and rows mostly stay in
 // L2 anyway), take the plain sampler: there the sort costs more than it
@@ -46,108 +50,147 @@ __device__ __forceinline__ uint64_t draw_r_of(uint64_t total, uint64_t seed, uin
 }
 
 // Bucket of every id of block b's run [b * per, (b + 1) * per) into bkt, and
-// the run's bucket counts into row b of hist.
+// the run's bucket counts into hist[bucket * kOrderMaxRuns + b] (per-warp
+// counters first).  Two draws per iteration, so two Philox chains overlap.
 template <int SAMPLER>
 __global__ void __launch_bounds__(kOrderThreads)
 k_order_count(uint64_t total, uint64_t kk, uint64_t seed, uint64_t first_id, int shift, uint64_t per,
-              uint32_t *hist, uint16_t *bkt) {
-    extern __shared__ uint32_t s_h[];
-    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) s_h[b] = 0;
+              uint32_t *hist, uint8_t *bkt) {
+    __shared__ uint32_t s_h[kOrderWarps][kOrderBuckets];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kOrderWarps * kOrderBuckets; i += kOrderThreads) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const uint64_t lo = (uint64_t)blockIdx.x * per;
     const uint64_t hi = lo + per < kk ? lo + per : kk;
-    for (uint64_t s = lo + threadIdx.x; s < hi; s += kOrderThreads) {
+    for (uint64_t s = lo + threadIdx.x; s < hi; s += 2 * kOrderThreads) {
+        const uint64_t s2 = s + kOrderThreads;
         const uint32_t c = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s) >> shift);
-        bkt[s] = static_cast<uint16_t>(c);
-        atomicAdd(s_h + c, 1u);
-    }
-    __syncthreads();
-    uint32_t *row = hist + (size_t)blockIdx.x * kOrderBuckets;
-    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) row[b] = s_h[b];
-}
-
-// For every bucket (one thread each): the runs' counts become exclusive
-// offsets within the bucket, and base[bucket] its total.  Eight rows are
-// loaded before any is rewritten, so their loads overlap.
-__global__ void __launch_bounds__(256)
-k_order_runs(int runs, uint32_t *hist, uint32_t *base) {
-    const int b = blockIdx.x * 256 + threadIdx.x;
-    if (b >= kOrderBuckets) return;
-    uint32_t run = 0;
-    uint32_t *p = hist + b;
-    int r = 0;
-    for (; r + 8 <= runs; r += 8) {
-        uint32_t c[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) c[i] = p[(size_t)(r + i) * kOrderBuckets];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            p[(size_t)(r + i) * kOrderBuckets] = run;
-            run += c[i];
+        const uint32_t c2 = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s2) >> shift);
+        bkt[s] = static_cast<uint8_t>(c);
+        atomicAdd(&s_h[warp][c], 1u);
+        if (s2 < hi) {
+            bkt[s2] = static_cast<uint8_t>(c2);
+            atomicAdd(&s_h[warp][c2], 1u);
         }
     }
-    for (; r < runs; r++) {
-        const uint32_t c = p[(size_t)r * kOrderBuckets];
-        p[(size_t)r * kOrderBuckets] = run;
-        run += c;
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kOrderWarps; w++) c += s_h[w][b];
+        hist[(size_t)b * kOrderMaxRuns + blockIdx.x] = c;
     }
-    base[b] = run;
 }
 
-// Exclusive prefix of the bucket totals, in place (one block).
-__global__ void __launch_bounds__(kOrderScanThreads)
-k_order_bases(uint32_t *base) {
-    extern __shared__ uint32_t s_v[];  // kOrderBuckets
-    __shared__ uint32_t s_warp[kOrderScanThreads / 32];
+// Exclusive prefix of v[0..kOrderBuckets) across the first kOrderBuckets
+// threads of the block (every thread must call it); returns thread t's
+// exclusive prefix and leaves the total in *total.
+__device__ __forceinline__ uint32_t bucket_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = t; i < kOrderBuckets; i += kOrderScanThreads) s_v[i] = base[i];
-    __syncthreads();
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kOrderPerThread; i++) sum += s_v[t * kOrderPerThread + i];
-    uint32_t x = sum;
+    uint32_t x = t < kOrderBuckets ? v : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) s_warp[warp] = x;
+    if (lane == 31 && warp < kOrderBuckets / 32) s_warp[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = s_warp[lane];
+    uint32_t before = 0, all = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        s_warp[lane] = w;
+    for (int w = 0; w < kOrderBuckets / 32; w++) {
+        const uint32_t sw = s_warp[w];
+        before += w < warp ? sw : 0u;
+        all += sw;
     }
     __syncthreads();
-    uint32_t run = x - sum + (warp ? s_warp[warp - 1] : 0u);
-#pragma unroll
-    for (int i = 0; i < kOrderPerThread; i++) {
-        const uint32_t c = s_v[t * kOrderPerThread + i];
-        s_v[t * kOrderPerThread + i] = run;
-        run += c;
-    }
-    __syncthreads();
-    for (int i = t; i < kOrderBuckets; i += kOrderScanThreads) base[i] = s_v[i];
+    *total = all;
+    return before + x - (t < kOrderBuckets ? v : 0u);
 }
 
-// Block b places its run of ids: cursors start at base[bucket] + the run's
-// offset within the bucket and advance with shared-memory atomics.
+// Block b (kOrderBuckets threads, 4 runs each): bucket b's run counts become
+// exclusive offsets within the bucket, and totals[b] its size.
+__global__ void __launch_bounds__(kOrderBuckets)
+k_order_offsets(int runs, uint32_t *hist, uint32_t *totals) {
+    static_assert(4 * kOrderBuckets == kOrderMaxRuns, "4 runs per thread");
+    __shared__ uint32_t s_warp[kOrderBuckets / 32];
+    uint32_t *p = hist + (size_t)blockIdx.x * kOrderMaxRuns + 4 * threadIdx.x;
+    uint32_t c[4], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        c[i] = 4 * threadIdx.x + i < runs ? p[i] : 0u;
+        sum += c[i];
+    }
+    uint32_t all;
+    uint32_t run = bucket_scan(sum, s_warp, &all);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (4 * threadIdx.x + i < runs) p[i] = run;
+        run += c[i];
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = all;
+}
+
+// Block b places its run of ids, kOrderTile at a time: each tile is first
+// counting-sorted by bucket in shared memory, then each bucket's ids are
+// written as one contiguous piece at the run's cursor for that bucket
+// (base[bucket] + the run's offset within it, advanced after every tile), so
+// the stores coalesce.  The buckets of the next tile are loaded while the
+// current one is placed.
 __global__ void __launch_bounds__(kOrderThreads)
-k_order_scatter(uint64_t kk, uint64_t per, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ base,
-                const uint16_t *__restrict__ bkt, uint32_t *ids) {
-    extern __shared__ uint32_t s_c[];
-    const uint32_t *row = hist + (size_t)blockIdx.x * kOrderBuckets;
-    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) s_c[b] = base[b] + row[b];
-    __syncthreads();
+k_order_scatter(uint64_t kk, uint64_t per, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals,
+                const uint8_t *__restrict__ bkt, uint32_t *ids) {
+    __shared__ uint32_t s_cur[kOrderBuckets], s_cnt[kOrderBuckets], s_off[kOrderBuckets];
+    __shared__ uint32_t s_warp[kOrderBuckets / 32];
+    __shared__ uint32_t s_id[kOrderTile];
+    __shared__ uint8_t s_b[kOrderTile];
+    const int t = threadIdx.x;
+    {
+        // the buckets' first positions: exclusive prefix of their totals
+        uint32_t all;
+        const uint32_t base = bucket_scan(t < kOrderBuckets ? totals[t] : 0u, s_warp, &all);
+        if (t < kOrderBuckets) s_cur[t] = base + hist[(size_t)t * kOrderMaxRuns + blockIdx.x];
+    }
     const uint64_t lo = (uint64_t)blockIdx.x * per;
     const uint64_t hi = lo + per < kk ? lo + per : kk;
-    for (uint64_t s = lo + threadIdx.x; s < hi; s += kOrderThreads) {
-        const uint32_t pos = atomicAdd(s_c + bkt[s], 1u);
-        ids[pos] = static_cast<uint32_t>(s);
+    uint32_t nxt[kOrderItems];
+#pragma unroll
+    for (int i = 0; i < kOrderItems; i++) {
+        const uint64_t q = lo + (uint64_t)i * kOrderThreads + t;
+        nxt[i] = q < hi ? static_cast<uint32_t>(bkt[q]) : static_cast<uint32_t>(kOrderBuckets);
+    }
+    for (uint64_t t0 = lo; t0 < hi; t0 += kOrderTile) {
+        if (t < kOrderBuckets) s_cnt[t] = 0;
+        uint32_t myb[kOrderItems], rank[kOrderItems];
+#pragma unroll
+        for (int i = 0; i < kOrderItems; i++) {
+            myb[i] = nxt[i];
+            const uint64_t q = t0 + kOrderTile + (uint64_t)i * kOrderThreads + t;
+            nxt[i] = q < hi ? static_cast<uint32_t>(bkt[q]) : static_cast<uint32_t>(kOrderBuckets);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kOrderItems; i++)
+            if (myb[i] < kOrderBuckets) rank[i] = atomicAdd(s_cnt + myb[i], 1u);
+        __syncthreads();
+        uint32_t all;
+        const uint32_t off = bucket_scan(t < kOrderBuckets ? s_cnt[t] : 0u, s_warp, &all);
+        if (t < kOrderBuckets) s_off[t] = off;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kOrderItems; i++) {
+            if (myb[i] < kOrderBuckets) {
+                const uint32_t p = s_off[myb[i]] + rank[i];
+                s_id[p] = static_cast<uint32_t>(t0 + (uint64_t)i * kOrderThreads + t);
+                s_b[p] = static_cast<uint8_t>(myb[i]);
+            }
+        }
+        __syncthreads();
+        for (uint32_t p = t; p < all; p += kOrderThreads) {
+            const uint32_t b = s_b[p];
+            ids[s_cur[b] + (p - s_off[b])] = s_id[p];
+        }
+        __syncthreads();
+        if (t < kOrderBuckets) s_cur[t] += s_cnt[t];
     }
 }
 
@@ -172,9 +215,9 @@ static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
     int shift = 0;
     while (shift < 63 && ((total - 1) >> shift) >= static_cast<uint64_t>(kOrderBuckets)) shift++;
     uint32_t *hist_runs = reinterpret_cast<uint32_t *>(scratch);
-    uint32_t *base = reinterpret_cast<uint32_t *>(scratch + kOrderHist);
+    uint32_t *totals = reinterpret_cast<uint32_t *>(scratch + kOrderHist);
     uint32_t *ids = reinterpret_cast<uint32_t *>(scratch + kOrderHeader);
-    uint16_t *bkt = reinterpret_cast<uint16_t *>(scratch + kOrderHeader + chunk * sizeof(uint32_t));
+    uint8_t *bkt = reinterpret_cast<uint8_t *>(scratch + kOrderHeader + chunk * sizeof(uint32_t));
     int per_sm = g->tune.blocks_per_sm;
     if (per_sm <= 0) {
         int occ = 0;
@@ -183,29 +226,24 @@ static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
         per_sm = occ > 0 ? occ : 1;
     }
     const uint64_t full = (uint64_t)g->sm_count * per_sm;
-    PS_CUDA_TRY(cudaFuncSetAttribute(k_order_count<SAMPLER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderSmem));
-    PS_CUDA_TRY(cudaFuncSetAttribute(k_order_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderSmem));
-    PS_CUDA_TRY(cudaFuncSetAttribute(k_order_bases, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderSmem));
     while (k > 0) {
         const uint64_t kk = k < chunk ? k : chunk;
         if (kk < kOrderMinChunk && g->tune.draw_order == 0) {
             const int rc = launch_sampler(g, SAMPLER, kk, seed, first_id, hist, s);
             if (rc) return rc;
         } else {
-            uint64_t runs = (uint64_t)g->sm_count * 2;
-            if (runs > (uint64_t)kOrderMaxBlocks) runs = kOrderMaxBlocks;
+            uint64_t runs = (uint64_t)g->sm_count * 2;  // one wave of the count kernel
+            if (runs > (uint64_t)kOrderMaxRuns) runs = kOrderMaxRuns;
             const uint64_t per = (kk + runs - 1) / runs;
             runs = (kk + per - 1) / per;
             uint64_t blocks = (kk + BLOCK - 1) / BLOCK;
             if (blocks > full) blocks = full;
-            k_order_count<SAMPLER><<<(unsigned)runs, kOrderThreads, kOrderSmem, s>>>(total, kk, seed, first_id, shift,
-                                                                                  per, hist_runs, bkt);
+            k_order_count<SAMPLER><<<(unsigned)runs, kOrderThreads, 0, s>>>(total, kk, seed, first_id, shift, per,
+                                                                         hist_runs, bkt);
             PS_LAUNCH_CHECK();
-            k_order_runs<<<kOrderBuckets / 256, 256, 0, s>>>(static_cast<int>(runs), hist_runs, base);
+            k_order_offsets<<<kOrderBuckets, kOrderBuckets, 0, s>>>(static_cast<int>(runs), hist_runs, totals);
             PS_LAUNCH_CHECK();
-            k_order_bases<<<1, kOrderScanThreads, kOrderSmem, s>>>(base);
-            PS_LAUNCH_CHECK();
-            k_order_scatter<<<(unsigned)runs, kOrderThreads, kOrderSmem, s>>>(kk, per, hist_runs, base, bkt, ids);
+            k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, bkt, ids);
             PS_LAUNCH_CHECK();
             k_sample_ordered<SAMPLER, BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id,
                                                                                     ids, hist);
@@ -239,8 +277,8 @@ static int ordered_s(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
     }
 }
 
-// Bytes per sample of a chunk: its id and its bucket.
-constexpr size_t kOrderPerSample = sizeof(uint32_t) + sizeof(uint16_t);
+// Bytes per sample of a chunk: its sorted id and its bucket.
+constexpr size_t kOrderPerSample = sizeof(uint32_t) + sizeof(uint8_t);
 
 size_t ordered_scratch_bytes(uint64_t k_chunk) {
     if (k_chunk == 0 || k_chunk > kOrderMaxChunk) return 0;
