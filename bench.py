@@ -7,9 +7,9 @@ tau / lambda prefixes + guide tables + hub bitmaps (ps_tau_prefix), k3
 samples of Alg. 1 and kc samples of Alg. 3 taken in edge-draw order
 (ps_sample_3paths_ordered / ps_sample_centered_ordered: the same counts as
 ps_sample_3paths / ps_sample_centered), the histograms read back and the
-estimates with error
-bars (ps_estimate).  value = (k3 + kc) samples per second of step time, timed
-with CUDA events on the launching stream, L2 flushed between steps.
+estimates with error bars (ps_estimate).  value = (k3 + kc) samples per
+second of step time, timed with CUDA events on the launching stream, L2
+flushed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
 
@@ -76,15 +76,16 @@ def measured_peak_hbm():
 
 def kernel_source_tag() -> str:
     h = hashlib.sha1()
-    for name in ("ps_sample.cuh", "ps_device.cuh", "ps_sample.cu"):
+    for name in ("ps_sample.cuh", "ps_device.cuh", "ps_sample.cu", "ps_order.cu"):
         with open(os.path.join(ROOT, "paper_1411_4942_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
 
 def ncu_traffic(workload: str):
-    """DRAM bytes per launch of the 3-path sampler from the committed ncu
-    summary, when it was taken on the current kernel source."""
+    """DRAM bytes of one 3-path sampler call (its draw sort and sampling
+    kernels) from the committed ncu summary, when it was taken on the current
+    kernel source."""
     path = os.path.join(ROOT, "profiles", f"ncu_k_sample_3path_{workload}.txt")
     try:
         text = open(path).read()
