@@ -50,3 +50,19 @@ def test_status_strings_and_workspace_sizes():
     t_off = ps.make_tuning(hub_count=-1, guide_log2_ratio=-1)
     assert ps.ps_graph_workspace_bytes(100000, 1000000, t_off) < ps.ps_graph_workspace_bytes(100000, 1000000)
     assert ps.ps_end_to_end_workspace_bytes(1000, 10000) > a
+
+
+def test_ordered_scratch_sizes():
+    """Scratch of the draw-ordered samplers: a fixed header plus 5 bytes per
+    sample of a chunk (its sorted id and its bucket); chunks of 1 .. 2^31."""
+    one = ps.ps_ordered_scratch_bytes(1)
+    assert one > 0
+    assert ps.ps_ordered_scratch_bytes(0) == 0
+    assert ps.ps_ordered_scratch_bytes((1 << 31) + 1) == 0
+    assert ps.ps_ordered_scratch_bytes(1 << 31) == one - 5 + 5 * (1 << 31)
+    for k in (2, 1000, 1 << 24):
+        assert ps.ps_ordered_scratch_bytes(k) == one + 5 * (k - 1)
+    # the tuning field that forces or disables the sort keeps the struct's size
+    import ctypes
+    assert ctypes.sizeof(ps.PsTuning) == 8 * 4
+    assert ps.make_tuning(draw_order=-1).draw_order == -1
