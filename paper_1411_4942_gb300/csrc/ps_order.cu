@@ -31,8 +31,8 @@ constexpr int kOrderTile = kOrderItems * kOrderThreads;   // ids a scatter block
 // hist[b * kOrderMaxRuns + run]: run counts, then offsets; then the bucket totals
 constexpr size_t kOrderHist = static_cast<size_t>(kOrderMaxRuns) * kOrderBuckets * sizeof(uint32_t);
 constexpr size_t kOrderHeader = kOrderHist + kOrderBuckets * sizeof(uint32_t);
-// after the header, per sample of a chunk: its bucket (uint8) and its
-// position in the sorted order (uint32 id offset)
+// after the header, per sample of a chunk: the sorted order (uint32 id
+// offsets from the chunk's first id), then each id's bucket (uint8)
 // By default (tuning draw_order 0) chunks below kOrderMinChunk samples, and
 // graphs below kOrderMinEdges edges (whose records and rows mostly stay in
 // L2 anyway), take the plain sampler: there the sort costs more than it
