@@ -599,3 +599,30 @@ def test_three_path_only_estimates():
     _, a, _, _ = O.estimate(og.W, og.Lambda, og.N1, h6, 5000, h4, 5000)
     _, b, _, _ = O.estimate(og.W, og.Lambda, og.N1, h6, 5000, h4, 5000, three_path_only=True)
     assert np.array_equal(a[:3], b[:3])
+
+
+def test_stored_rmat20_exact_counts_are_consistent():
+    """The stored exact counts of the R-MAT-20 benchmark graph (written by
+    tests/golden/make_exact_rmat20.py from the oracle alone) satisfy Eq. (1)
+    between the non-induced N and the induced C, N_1 = sum_v C(d_v, 3) from the
+    degrees, and N_2 <= W (N_2 = W - 3T, Section 3) with W from the degrees of
+    every edge's endpoints."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "exact_counts_rmat20.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/exact_counts_rmat20.json not written yet")
+    with open(path) as f:
+        ref = json.load(f)
+    N = np.array(ref["N"], dtype=object)
+    C = np.array(ref["C"], dtype=object)
+    A = O.EQ1_MATRIX.astype(object)
+    assert (A.dot(C) == N).all()
+    g = gg.rmat20()
+    deg = np.diff(g.off).astype(object)
+    assert N[0] == sum(d * (d - 1) * (d - 2) // 6 for d in deg)
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    up = src < g.col
+    d = np.diff(g.off).astype(np.int64)
+    W = int(((d[src[up]] - 1) * (d[g.col[up]] - 1)).sum())
+    assert 0 <= W - N[1] and (W - N[1]) % 3 == 0
