@@ -415,6 +415,7 @@ class Graph:
             ps_graph_free(self.handle)
             self.handle = None
         self.workspace = None
+        self._order_scratch = None
 
     def __del__(self):
         try:
