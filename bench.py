@@ -9,12 +9,19 @@ samples of Alg. 1 and kc samples of Alg. 3 taken in edge-draw order
 ps_sample_3paths / ps_sample_centered), the histograms read back and the
 estimates with error bars (ps_estimate).  value = (k3 + kc) samples per
 second of step time, timed with CUDA events on the launching stream, L2
-flushed between steps.
+flushed between steps.  The default workload is the 3M-vertex, 117M-edge
+social-network-shaped graph (k = 2^27 + 2^26 samples per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+                    [--workload social3m|rmat20|chung_lu_5k|batched512|served64]
 
-Under torchrun each rank runs the same workload on its own GPU with its own
-range of sample ids (weak scaling; no collective on the data path).
+Under torchrun each rank samples its own contiguous range of sample ids on its
+own replica of the graph (weak scaling); the only exchange is the per-step sum
+of the 10 histogram words (shard.combine_histograms), after which rank 0's
+estimates cover every rank's samples.
+
+--impl reference times the oracle (plain C on the host cores) on the same
+workload: its prepare once, then every step a new bounded range of ids.
 """
 from __future__ import annotations
 
@@ -41,8 +48,13 @@ SECTOR = 32
 # one 32-byte sector per random access): 3-path = edge draw, edge record,
 # both endpoint offsets, the two neighbour reads and three adjacency lookups
 BYTES_3PATH = 9 * SECTOR
-# samples per chunk of the draw-ordered samplers
-ORDER_CHUNK = 1 << 24
+# largest chunk of the draw-ordered samplers (their scratch is 5 B per sample
+# of a chunk); by default one chunk holds all of a call's samples up to this
+MAX_ORDER_CHUNK = 1 << 27
+# the load step's streaming bytes per edge in the O(m) preprocessing model:
+# 8 B per stored arc (its input column read, its relabelled column written;
+# two arcs per edge) plus the two uint64 prefixes, 32 B
+BYTES_LOAD_PER_EDGE = 48
 
 
 def workloads():
@@ -188,51 +200,144 @@ def reduce_max(x: float, world: int, device) -> float:
 
 # ------------------------------------------------------------ CPU baseline
 
-def oracle_rate(g, wl, slice_k: int, repeats: int = 1):
-    """The oracle (plain C, all host cores for the sampling loops) on a bounded
-    sample of the workload: the full prepare once, then `slice_k` sample ids
-    of each sampler, scaled linearly to the workload's k3 and kc."""
+# Bounded slices of the workload that the oracle samples (ids from 0 of each
+# sampler, the same ids on every repeat), as (label, threads, repeats, k3, kc);
+# threads 0 = every host core.  About 10-20 s of CPU work in all.
+ORACLE_SLICES = [("all_cores", 0, 5, 1 << 22, 1 << 21), ("one_core", 1, 3, 1 << 19, 1 << 18)]
+# per step of the reference arm: this many ids of each sampler (2:1 as k3:kc
+# of the 3M-vertex workload), every step a new id range
+REFERENCE_SLICE = (1 << 22, 1 << 21)
+
+
+def _oracle_worker(conn, off, col, seed, slices):
+    """The oracle in its own process: its prepare (validation, relabelling,
+    edge table and prefixes) at once, so it overlaps the GPU arm's set-up;
+    then, on request, the bounded sampling slices, timed."""
+    sys.path.insert(0, ROOT)
     import oracle as O
-    threads = max(1, O.max_threads())
     t0 = time.perf_counter()
-    og = O.prepare(g.off, g.col)
-    t_prep = time.perf_counter() - t0
-    t3 = tc = 0.0
-    for r in range(repeats):
-        t0 = time.perf_counter()
-        O.sample_3paths(og, slice_k, wl["seed"], r * slice_k, threads=threads)
-        t3 += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        O.sample_centered(og, slice_k, wl["seed"], r * slice_k, threads=threads)
-        tc += time.perf_counter() - t0
-    t3 /= repeats
-    tc /= repeats
-    total = t_prep + t3 * wl["k3"] / slice_k + tc * wl["kc"] / slice_k
+    og = O.prepare(off, col)
+    prep_s = time.perf_counter() - t0
+    conn.send({"prepare_s": prep_s, "W": og.W, "Lambda": og.Lambda, "N1": og.N1})
+    if conn.recv() != "go":
+        return
+    all_cores = max(1, O.max_threads())
+    out = {"prepare_s": prep_s, "host_cores": all_cores, "slices": {}}
+    for label, threads, reps, s3, sc in slices:
+        th = threads or all_cores
+        t3, tc = [], []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            h6 = O.sample_3paths(og, s3, seed, 0, threads=th)
+            t3.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            h4 = O.sample_centered(og, sc, seed, 0, threads=th)
+            tc.append(time.perf_counter() - t0)
+        out["slices"][label] = {
+            "threads": th, "repeats": reps, "k3": s3, "kc": sc,
+            "s_3path_median": statistics.median(t3), "s_centred_median": statistics.median(tc),
+            "hist6": [int(x) for x in h6], "hist4": [int(x) for x in h4]}
+    conn.send(out)
+
+
+class OracleLeg:
+    """The CPU baseline of the benchmark line: the oracle as it stands, on the
+    host cores, on bounded slices of the same workload.  Started (spawned)
+    before the GPU arm touches CUDA; its slices run after the timed region."""
+
+    def __init__(self, g, seed, slices, k3, kc):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.slices = [(lb, th, reps, min(s3, k3), min(sc, kc)) for lb, th, reps, s3, sc in slices]
+        self.proc = ctx.Process(target=_oracle_worker, args=(child, g.off, g.col, seed, self.slices),
+                                daemon=True)
+        self.proc.start()
+
+    def run(self):
+        ready = self.conn.recv()
+        self.conn.send("go")
+        res = self.conn.recv()
+        res.update({k: ready[k] for k in ("W", "Lambda", "N1")})
+        self.proc.join(timeout=60)
+        return res
+
+    def stop(self):
+        try:
+            self.conn.send("stop")
+        except (OSError, BrokenPipeError):
+            pass
+        self.proc.join(timeout=10)
+        if self.proc.is_alive():
+            self.proc.terminate()
+
+
+def cpu_baseline_line(res):
+    """cpu_baseline of the JSON line from the oracle leg's timings: value =
+    the oracle's sampling rate on all host cores over the workload's mix of
+    the two samplers (its prepare is timed separately, once)."""
+    a = res["slices"]["all_cores"]
+    o = res["slices"]["one_core"]
+    rate = lambda s: (s["k3"] + s["kc"]) / (s["s_3path_median"] + s["s_centred_median"])  # noqa: E731
     return {
-        "value": (wl["k3"] + wl["kc"]) / total, "unit": UNIT, "cores": threads, "kind": "oracle",
-        "sample": (f"oracle prepare (validate, relabel, edge table, prefixes) on the full graph "
-                   f"once ({t_prep:.2f} s) + {slice_k} ids of each sampler on {threads} threads "
-                   f"({t3:.3f} s, {tc:.3f} s), scaled linearly to k3={wl['k3']}, kc={wl['kc']}"),
-        "seconds_full_workload": total,
+        "value": rate(a), "unit": UNIT, "cores": a["threads"], "kind": "oracle",
+        "sample": (f"oracle sampling loops, ids [0, {a['k3']}) of Alg. 1 and [0, {a['kc']}) of "
+                   f"Alg. 3 on {a['threads']} threads, median of {a['repeats']} "
+                   f"({a['s_3path_median']:.3f} s + {a['s_centred_median']:.3f} s); its prepare "
+                   f"(validate, relabel, edge table, prefixes) of the whole graph once, "
+                   f"{res['prepare_s']:.1f} s, not in value; nothing extrapolated"),
+        "prepare_s": res["prepare_s"],
+        "one_core": {"samples_per_s": rate(o), "k3": o["k3"], "kc": o["kc"], "repeats": o["repeats"],
+                     "s_3path_median": o["s_3path_median"], "s_centred_median": o["s_centred_median"]},
+        "all_cores": {"samples_per_s": rate(a), "3path_samples_per_s": a["k3"] / a["s_3path_median"],
+                      "centred_samples_per_s": a["kc"] / a["s_centred_median"]},
     }
+
+
+def workload_config(name, wl, n, m, W, Lambda, d_max, world):
+    """The `config` object of both arms' JSON lines (the same dict)."""
+    return {"workload": f"{name}: {wl['desc']}", "n": int(n), "m": int(m), "W": int(W),
+            "Lambda": int(Lambda), "d_max": int(d_max), "k3": wl["k3"], "kc": wl["kc"],
+            "samples_per_step": wl["k3"] + wl["kc"],
+            "l2": ("a 256 MB buffer is written between steps, outside the step events, and the "
+                   "graph's device arrays are larger than L2"),
+            "parallelism": f"replicas x{world}, contiguous sample-id ranges, one histogram sum"}
 
 
 # --------------------------------------------------------------- GPU arm
 
 def run_cuda(args):
+    rank, world, local = dist_env()
+    wl = workloads()[args.workload]
+    g = wl["make"]()
+    # the oracle leg starts before this process initialises CUDA
+    leg = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        leg = OracleLeg(g, wl["seed"], ORACLE_SLICES, wl["k3"], wl["kc"])
+    try:
+        _run_cuda(args, g, wl, leg)
+    finally:
+        if leg is not None:
+            leg.stop()
+
+
+def _run_cuda(args, g, wl, leg):
     import torch
     from paper_1411_4942_gb300 import pathsample as ps
+    from paper_1411_4942_gb300 import shard
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     dist_init(world, "nccl")
-    wl = workloads()[args.workload]
-    g = wl["make"]()
     k3, kc, seed = wl["k3"], wl["kc"], wl["seed"]
-    first3 = rank * k3  # weak scaling: every rank its own id range
-    firstc = rank * kc
+    # weak scaling: the job is world x (k3 + kc) samples, every rank one
+    # contiguous range of ids of each sampler, histograms summed per step
+    first3, n3 = shard.shard_range(world * k3, rank, world)
+    firstc, nc = shard.shard_range(world * kc, rank, world)
+    assert n3 == k3 and nc == kc
     ps.load_library()
+    chunk = args.order_chunk or min(max(k3, kc, 1), MAX_ORDER_CHUNK)
 
     stream = torch.cuda.Stream(device)
     sp = stream.cuda_stream
@@ -242,8 +347,8 @@ def run_cuda(args):
         nb = ps.ps_graph_workspace_bytes(g.n, g.nnz)
         ws = torch.empty(nb, dtype=torch.uint8, device=device)
         hist = torch.zeros(16, dtype=torch.int64, device=device)
-        # scratch of the draw-ordered samplers: one chunk of max(k3, kc) samples
-        osb = ps.ps_ordered_scratch_bytes(min(max(k3, kc, 1), ORDER_CHUNK))
+        # scratch of the draw-ordered samplers: one chunk
+        osb = ps.ps_ordered_scratch_bytes(chunk)
         oscr = torch.empty(osb, dtype=torch.uint8, device=device)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -268,11 +373,14 @@ def run_cuda(args):
                                                     oscr.data_ptr(), osb, sp),
                       "ps_sample_centered_ordered", (ps.PS_OK, ps.PS_NO_PATHS))
             e[3].record(stream)
+            shard.combine_histograms(hist)
             hh = hist.cpu().numpy().astype(np.uint64)
-            rc, est, lo, hi = ps.ps_estimate(st, hh[:6], k3, hh[8:12], kc, 0.01)
+            rc, est, lo, hi = ps.ps_estimate(st, hh[shard.HIST6], world * k3, hh[shard.HIST4],
+                                             world * kc, 0.01)
             e[4].record(stream)
             ps.ps_graph_free(h)
-            last.update(stats=st, hist6=hh[:6].copy(), hist4=hh[8:12].copy(), est=est, lo=lo, hi=hi)
+            last.update(stats=st, hist6=hh[shard.HIST6].copy(), hist4=hh[shard.HIST4].copy(),
+                        est=est, lo=lo, hi=hi)
 
         for i in range(args.warmup):
             flush.zero_()
@@ -307,9 +415,14 @@ def run_cuda(args):
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_3PATH * k3 / (avg3 / 1e3) / 1e9
     h4 = last["hist4"]
-    f_c = 1.0 - float(h4[0]) / kc if kc else 0.0
+    f_c = 1.0 - float(h4[0]) / (world * kc) if kc else 0.0
     bytes_c = (7 + 2 * f_c) * SECTOR
     achieved_c = bytes_c * kc / (avgc / 1e3) / 1e9
+    st = last["stats"]
+    # the load step against streaming: 48 B per edge (the degree, offset and
+    # column reads of the input, the records and both prefixes written)
+    load_bytes = BYTES_LOAD_PER_EDGE * st.m
+    achieved_load = load_bytes / (statistics.mean(prep_ms) / 1e3) / 1e9
     traffic = ncu_traffic(args.workload)
 
     # end to end through the host-buffer call (inputs copied from pinned memory every step)
@@ -337,24 +450,21 @@ def run_cuda(args):
         e2e = {"value": world * args.steps * (k3 + kc) / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * e2e_s / args.steps}
+        del ws2
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_rate(g, wl, args.cpu_slice)
-        cpu.pop("seconds_full_workload", None)
+    if leg is not None:
+        res = leg.run()
+        cpu = cpu_baseline_line(res)
+        cpu["oracle_equals_gpu"] = _check_oracle_slices(g, wl, res, device)
 
     if rank == 0:
-        st = last["stats"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl['desc']}", "n": g.n, "m": g.m,
-                       "W": int(st.W), "Lambda": int(st.Lambda), "d_max": int(st.d_max),
-                       "k3": k3, "kc": kc, "samples_per_step": k3 + kc,
-                       "l2": "256 MB buffer written between steps (outside the step events); "
-                             "the graph's device arrays are ~1.2 GB, larger than L2",
-                       "parallelism": f"replicas x{world}, disjoint sample-id ranges"},
+            "config": workload_config(args.workload, wl, g.n, st.m, st.W, st.Lambda, st.d_max,
+                                      world),
             "breakdown_ms": {"load_and_prefix": statistics.mean(prep_ms),
                              "sample_3path": avg3, "sample_centred": avgc,
                              "readback_and_estimate": statistics.mean(est_ms)},
@@ -369,6 +479,11 @@ def run_cuda(args):
             "roofline_centred": {"bound": "hbm", "achieved": achieved_c, "peak": peak,
                                  "unit": "GB/s", "frac": achieved_c / peak,
                                  "bytes_per_sample": bytes_c, "centred_fraction": f_c},
+            "roofline_load": {"bound": "hbm", "achieved": achieved_load, "peak": peak,
+                              "unit": "GB/s", "frac": achieved_load / peak,
+                              "bytes_per_edge": BYTES_LOAD_PER_EDGE,
+                              "kernel": "ps_load_csr + ps_tau_prefix (all kernels, sorts included)"},
+            "order_chunk": chunk,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,
             "wall_s_timed_region": t_wall,
@@ -379,6 +494,22 @@ def run_cuda(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _check_oracle_slices(g, wl, res, device):
+    """The oracle's slice histograms against the library's for the same ids
+    (the draw-ordered samplers the step times), and W / Lambda / N_1."""
+    import torch
+    from paper_1411_4942_gb300 import pathsample as ps
+    G = ps.Graph(g.off, g.col, device=device)
+    ok = (int(G.stats.W), int(G.stats.Lambda), G.stats.N1) == (res["W"], res["Lambda"], res["N1"])
+    for sl in res["slices"].values():
+        h6 = G.sample_3paths_ordered(sl["k3"], wl["seed"]).cpu().numpy()[:6]
+        h4 = G.sample_centered_ordered(sl["kc"], wl["seed"]).cpu().numpy()[:4]
+        ok = ok and [int(x) for x in h6] == sl["hist6"] and [int(x) for x in h4] == sl["hist4"]
+    torch.cuda.synchronize(device)
+    G.close()
+    return bool(ok)
 
 
 # ------------------------------------------------- batched and served arms
@@ -578,7 +709,9 @@ def run_served(args):
 # ---------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The oracle on the host cores, as it stands, on the same workload."""
+    """The oracle on the host cores, as it stands, on the same workload: its
+    prepare of the whole graph once, then every step a new bounded id range of
+    both samplers on all host cores, each step timed as it ran."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -594,27 +727,34 @@ def run_reference(args):
     t0 = time.perf_counter()
     og = O.prepare(g.off, g.col)
     t_prep = time.perf_counter() - t0
-    slice_k = args.cpu_slice
-    times = []
+    s3, sc = min(REFERENCE_SLICE[0], wl["k3"]), min(REFERENCE_SLICE[1], wl["kc"])
+    times, hists = [], None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        O.sample_3paths(og, slice_k, wl["seed"], i * slice_k, threads=threads)
-        O.sample_centered(og, slice_k, wl["seed"], i * slice_k, threads=threads)
+        h6 = O.sample_3paths(og, s3, wl["seed"], i * s3, threads=threads)
+        h4 = O.sample_centered(og, sc, wl["seed"], i * sc, threads=threads)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    per_pair = statistics.mean(times)  # slice_k ids of each sampler
-    full_s = t_prep + per_pair * (wl["k3"] + wl["kc"]) / (2 * slice_k)
-    value = (wl["k3"] + wl["kc"]) / full_s
+        if i == 0:
+            hists = ([int(x) for x in h6], [int(x) for x in h4])
+    total_s = sum(times)
+    value = args.steps * (s3 + sc) / total_s
+    d_max = int(np.diff(g.off).max()) if g.n else 0
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full_s,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": f"{args.workload}: {wl['desc']}", "n": g.n,
-                                        "m": g.m, "k3": wl["k3"], "kc": wl["kc"]},
+        "data": "synthetic",
+        "config": workload_config(args.workload, wl, g.n, og.m, og.W, og.Lambda, d_max, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": (f"oracle prepare on the full graph once ({t_prep:.2f} s); "
-                                    f"each step samples {slice_k} ids of each sampler on "
-                                    f"{threads} threads; scaled linearly to k3 + kc")},
+                         "sample": (f"every step: oracle sampling loops over a new range of "
+                                    f"{s3} ids of Alg. 1 and {sc} of Alg. 3 on {threads} threads, "
+                                    f"timed as run (no extrapolation); the oracle's prepare of the "
+                                    f"whole graph ran once before the steps ({t_prep:.1f} s) and "
+                                    f"is not in value"),
+                         "prepare_s": t_prep},
+        "samples_per_step": s3 + sc,
+        "step0_hist6": hists[0], "step0_hist4": hists[1],
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -626,9 +766,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--workload", default="rmat20",
+    ap.add_argument("--workload", default="social3m",
                     choices=["rmat20", "chung_lu_5k", "social3m", "batched512", "served64"])
-    ap.add_argument("--cpu-slice", type=int, default=1 << 20)
+    ap.add_argument("--order-chunk", type=int, default=0,
+                    help="samples per chunk of the draw-ordered samplers (0: all of a call's "
+                         f"samples, up to {MAX_ORDER_CHUNK})")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="served64: number of requests")

@@ -107,6 +107,8 @@ size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
  * stream and may still be running when the call returns: ps_tau_prefix
  * orders it before everything it queues on its own stream, and
  * ps_graph_free waits for it.  On error *out is NULL and the status is
+ * PS_ERR_TIMEOUT (a bounded device wait of one of the scans expired, which
+ * makes every other finding of the call unreliable, so it comes first) /
  * PS_ERR_ARG / PS_ERR_NOT_SIMPLE / PS_ERR_ASYMMETRIC (highest-priority
  * first) or PS_ERR_WORKSPACE / PS_ERR_CUDA. */
 int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_col,
@@ -366,12 +368,17 @@ int ps_count_exact(const ps_graph *g, void *d_scratch, size_t scratch_bytes, ps_
  * exactly in uint64 for i < count (device arrays; outputs may not alias the
  * inputs).  The scan's scratch is a fixed array of about 2.3 MB inside the
  * library that every GPU using the library keeps until the process exits;
- * no device memory is allocated or freed and no allocating library routine
- * is called.  The first call on each device looks up that array's device
- * address (once per device, with that device current); make that first call
- * before any stream capture.  All calls share the one array, so calls that
- * overlap on the GPU (different streams or threads at once) race and give
- * wrong results; issue them one after another.  Synchronises `stream`.
+ * the call allocates and frees no device memory and calls no allocating
+ * library routine.  The first call on each device does the set-up: it looks
+ * up that array's device address (with that device current; again after a
+ * device reset, which gives the device a new context), and under CUDA's
+ * default lazy loading that first call is also when the driver loads the
+ * library's device code on the device and sets the array aside.  So make the
+ * first call on each device at start-up, before requests are in flight and
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call clears what must start at zero), so calls
+ * that overlap on the GPU (different streams or threads at once) race and
+ * give wrong results; issue them one after another.  Synchronises `stream`.
  * Returns PS_ERR_TOO_LARGE (touching nothing) when count exceeds
  * PS_PREFIX_STATIC_MAX_ITEMS, PS_ERR_OVERFLOW when a sum does not fit in
  * 64 bits, PS_ERR_ARG for a negative count or a missing pointer. */

@@ -139,7 +139,21 @@ class BatchRunner:
         self.graph.replay()
 
     def histograms(self) -> np.ndarray:
-        return self.d_hist.cpu().numpy().reshape(-1, 6).astype(np.uint64)
+        """The slots' histograms after the last launch; raises if that launch
+        skipped items (a graph whose adjacency variant differs from the one
+        the descriptor table records: its samples would be missing)."""
+        import torch
+        both = torch.cat([self.d_hist, self.d_counter.to(torch.int64)]).cpu().numpy()
+        check_skipped(int(both[-1]))
+        return both[:-2].reshape(-1, 6).astype(np.uint64)
+
+
+def check_skipped(skipped: int):
+    """The batched kernel counts the items it skipped (counter word 1);
+    any skipped item means histograms that do not sum to their k."""
+    if skipped:
+        raise RuntimeError(f"the batched launch skipped {skipped} work items: the descriptor "
+                           "table's adjacency variant does not match a graph's")
 
 
 def run_plain(gset: GraphSet, requests, stream=None):

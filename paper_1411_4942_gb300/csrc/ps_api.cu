@@ -64,12 +64,16 @@ int get_side_streams(int device, cudaStream_t out[2]) {
     return PS_OK;
 }
 
+// A scan whose bounded wait expired put identity in place of a predecessor's
+// sum, so every later value of that call -- and any flag raised from them,
+// such as a spurious overflow or asymmetry -- is unreliable: the timeout is
+// reported first.
 int flags_to_status(uint64_t f) {
+    if (f & F_TIMEOUT) return PS_ERR_TIMEOUT;
     if (f & F_ARG) return PS_ERR_ARG;
     if (f & F_NOT_SIMPLE) return PS_ERR_NOT_SIMPLE;
     if (f & F_ASYM) return PS_ERR_ASYMMETRIC;
     if (f & F_OVERFLOW) return PS_ERR_OVERFLOW;
-    if (f & F_TIMEOUT) return PS_ERR_TIMEOUT;
     return PS_OK;
 }
 

@@ -3,6 +3,8 @@
 // prefixes) for callers that cannot allocate device memory.  Its scratch --
 // the scan's tile flags, tile sums and tile counter -- lives in one
 // fixed-size array in this file instead of a caller's workspace.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ps_internal.h"
@@ -25,20 +27,61 @@ static __device__ __align__(256) unsigned char g_prefix_scratch[kScratchBytes];
 
 std::mutex g_mutex;
 constexpr int kMaxDevices = 128;
-void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per
-// device (the host-side name is only a stand-in for it).
+// The array's device address, looked up once per device and context: a
+// process that resets a device (or releases its primary context) gets a new
+// context, in which the library's device code is loaded again and the array
+// may sit elsewhere, so the cached address is only reused under the context
+// it was read in.  Context ids (unlike context handles) are never reused.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the context current on this thread; 0 when there is none or the
+// driver cannot say (the address is then looked up again).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the array on the current device (the host-side name is
+// only a stand-in for it).
 int scratch_address(void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    ScratchAddr &c = g_scratch_addr[dev];
+    if (id == 0 || c.ctx_id != id || !c.ptr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_prefix_scratch) != cudaSuccess || !p) return PS_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+        // the lookup itself makes the device's context current when none was
+        c.ctx_id = current_context_id();
+        c.ptr = p;
     }
-    *out = g_scratch_addr[dev];
+    *out = c.ptr;
     return PS_OK;
 }
 

@@ -23,7 +23,7 @@ import time
 import numpy as np
 
 from . import pathsample as ps
-from .batch import LaunchConfig, SAMPLER_3PATH, SAMPLER_CENTRED, order_by_graph
+from .batch import LaunchConfig, SAMPLER_3PATH, SAMPLER_CENTRED, check_skipped, order_by_graph
 
 
 @dataclasses.dataclass
@@ -157,6 +157,9 @@ class Server:
         self.streams = [torch.cuda.Stream(dev) for _ in range(streams)]
         self.d_hist = torch.zeros(12 * self.max_active, dtype=torch.int64, device=dev)
         self.counters = [torch.zeros(2, dtype=torch.int32, device=dev) for _ in self.streams]
+        # items the batched kernel skipped, summed per launch stream (each
+        # stream adds its own launch's count after the kernel)
+        self.skipped = torch.zeros(len(self.streams), dtype=torch.int64, device=dev)
         self.free_slots = list(range(self.max_active))[::-1]
         self.tuning = self.cfg.tuning()
         self.iterations = 0
@@ -169,7 +172,9 @@ class Server:
         import torch
         self._zero_slots([0])
         sel = torch.tensor([0], dtype=torch.int64, device=self.pool.device)
-        self.d_hist.view(self.max_active, 12).index_select(0, sel).cpu()
+        torch.cat([self.d_hist.view(self.max_active, 12).index_select(0, sel).flatten(),
+                   self.skipped]).cpu()
+        self.skipped[0:1] += self.counters[0][1:2]
         torch.from_numpy(np.zeros(16, dtype=np.uint8)).pin_memory().to(self.pool.device, non_blocking=True)
         torch.cuda.Event().record(self.streams[0])
         torch.cuda.synchronize(self.pool.device)
@@ -193,6 +198,7 @@ class Server:
                                              self.d_hist.data_ptr(), self.counters[si].data_ptr(),
                                              self.tuning, s)
             ps._check(rc, "ps_batch_sample_prepared")
+            self.skipped[si:si + 1] += self.counters[si][1:2]
             ev = torch.cuda.Event()
             ev.record(s)
         self.iterations += 1
@@ -243,7 +249,9 @@ class Server:
                     hist = self.d_hist.view(self.max_active, 12)
                     sel = torch.tensor([a.slot for a in done], dtype=torch.int64,
                                        device=self.pool.device)
-                    rows = hist.index_select(0, sel).cpu().numpy().astype(np.uint64)
+                    both = torch.cat([hist.index_select(0, sel).flatten(), self.skipped]).cpu().numpy()
+                    check_skipped(int(both[-len(self.streams):].sum()))
+                    rows = both[:-len(self.streams)].reshape(-1, 12).astype(np.uint64)
                     t_fin = time.perf_counter() - t0
                     for a, row in zip(done, rows):
                         g = self.pool.loaded[a.req.graph]
@@ -290,6 +298,7 @@ class Server:
                 gap = pending[0].arrival - now
                 if gap > 0:
                     time.sleep(min(gap, 1e-3))
+        check_skipped(int(self.skipped.sum().item()))
         makespan = (max(r.finished for r in results)) if results else 0.0
         lat = np.array([r.latency for r in results]) if results else np.zeros(1)
         report = {
