@@ -1,10 +1,12 @@
 """Batched launch and serving loop on the GPU: every request's class counts
-must equal those of the same request run alone with the plain calls (integer
-counts, so bit for bit; estimates to 1e-12 relative)."""
+must equal those of the oracle for the same (graph, k, seed, ids) and of the
+same request run alone with the plain calls (integer counts, so bit for bit;
+estimates to 1e-12 relative)."""
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -102,3 +104,66 @@ def test_served_results_equal_requests_alone(realtime):
         h6, h4, est = by_id[r.rid]
         assert r.hist6.tolist() == h6.tolist() and r.hist4.tolist() == h4.tolist()
         np.testing.assert_allclose(r.est, est, rtol=1e-12)
+
+
+def _oracle_hist(og, sampler, k, seed, first_id=0):
+    threads = max(1, min(16, O.max_threads()))
+    if sampler == B.SAMPLER_3PATH:
+        return O.sample_3paths(og, k, seed, first_id, threads=threads) if og.W else np.zeros(6, np.uint64)
+    h = O.sample_centered(og, k, seed, first_id, threads=threads) if og.Lambda else np.zeros(4, np.uint64)
+    return np.concatenate([h, np.zeros(2, np.uint64)])
+
+
+def test_batched_slots_equal_oracle():
+    """One batch over nine graphs of uneven size -- eight R-MAT graphs of
+    scales 8..12 (the three adjacency variants mixed) and one R-MAT scale-17
+    graph of over 2^20 edges -- with per-request k and seeds, ids starting past
+    2^32 for some requests: every slot equals the oracle's histogram."""
+    rs = np.random.default_rng(31)
+    hosts = [gg.rmat(int(rs.integers(8, 13)), float(rs.integers(8, 33)), seed=700 + i) for i in range(8)]
+    hosts.append(gg.rmat(17, 16.0, seed=777))
+    assert hosts[-1].m >= 1 << 20
+    graphs = [ps.Graph(h.off, h.col, tuning=ps.make_tuning(adjacency=(ps.ADJ_HASH, ps.ADJ_SEARCH,
+                                                                       ps.ADJ_VTAB)[i % 3]))
+              for i, h in enumerate(hosts)]
+    gset = B.GraphSet(graphs)
+    reqs = B.random_requests(rs, len(graphs), log2_k=(10, 16))
+    for i, r in enumerate(reqs):
+        if i % 3 == 1:
+            r.first_id = (1 << 32) - 1000 + i
+    run = B.BatchRunner(gset, reqs, B.LaunchConfig(256, 1 << 12, 0))
+    run.launch()
+    torch.cuda.synchronize()
+    got = run.histograms()
+    ogs = [O.prepare(h.off, h.col) for h in hosts]
+    for r in reqs:
+        want = _oracle_hist(ogs[r.graph], r.sampler, r.k, r.seed, r.first_id)
+        assert got[r.slot].tolist() == want.tolist(), (r, got[r.slot], want)
+
+
+@pytest.mark.parametrize("realtime", [True, False])
+def test_served_results_equal_oracle(realtime):
+    """Every served request (mixed graphs, evictions forced by the budget,
+    Poisson arrivals replayed or all at once) against the oracle: both
+    histograms bit for bit and the estimates to 1e-12."""
+    sources = _sources(6)
+    sizes = [ps.ps_graph_workspace_bytes(len(o) - 1, len(c)) for o, c in sources.values()]
+    budget = int(sum(sizes) * 0.6)
+    pool = S.GraphPool(sources, budget)
+    server = S.Server(pool, quantum=1 << 13, max_active=64, cfg=B.LaunchConfig(256, 1 << 12))
+    rs = np.random.default_rng(13)
+    reqs = S.poisson_requests(rs, list(sources), 60, 4000.0, log2_k=(8, 15))
+    results, report = server.run(reqs, realtime=realtime)
+    assert report["graph_evictions"] > 0 and len(results) == len(reqs)
+    ogs = {key: O.prepare(off, col) for key, (off, col) in sources.items()}
+    by_id = {r.rid: r for r in reqs}
+    for res in results:
+        req = by_id[res.rid]
+        og = ogs[req.graph]
+        h6 = _oracle_hist(og, B.SAMPLER_3PATH, req.k, req.seed)
+        h4 = _oracle_hist(og, B.SAMPLER_CENTRED, req.k, req.seed)[:4]
+        assert res.hist6.tolist() == h6.tolist() and res.hist4.tolist() == h4.tolist()
+        _, est, lo, hi = O.estimate(og.W, og.Lambda, og.N1, h6, req.k, h4, req.k, 0.01)
+        np.testing.assert_allclose(res.est, est, rtol=1e-12)
+        np.testing.assert_allclose(res.lo, lo, rtol=1e-12)
+        np.testing.assert_allclose(res.hi, hi, rtol=1e-12)

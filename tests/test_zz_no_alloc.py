@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -62,3 +63,42 @@ def test_static_prefix_limits():
     assert rc == ps.PS_ERR_OVERFLOW
     rc, pa, pb = _run_static(np.arange(10, dtype=np.uint64), np.ones(10, dtype=np.uint64))
     assert rc == ps.PS_OK and pa.tolist() == np.cumsum(np.arange(10)).tolist()
+
+
+def test_static_prefix_equals_oracle_prefixes():
+    # the oracle's own tau / lambda weights in, its own prefixes expected out
+    # (two graphs, two calls in a row)
+    for g in (gg.chung_lu(4000, 12.0, 2.2, 250.0, 17), gg.rmat(14, 10.0, seed=23)):
+        og = O.prepare(g.off, g.col)
+        rc, pa, pb = _run_static(og.tau, og.lam)
+        assert rc == ps.PS_OK
+        assert np.array_equal(pa, og.ptau) and np.array_equal(pb, og.plam)
+
+
+def test_static_prefix_allocates_nothing():
+    """The call's defining property: once the first call on the device has
+    done its set-up, calls of any size leave the device's free memory exactly
+    as it was (no cudaMalloc, no allocating library routine, no growth of a
+    pool).  Every buffer is allocated before the first reading."""
+    sizes = (1, 4095, 1 << 16, 3 << 18)
+    bufs = []
+    for n in sizes:
+        a = torch.arange(n, dtype=torch.int64, device="cuda")
+        b = torch.ones(n, dtype=torch.int64, device="cuda")
+        bufs.append((a, b, torch.empty_like(a), torch.empty_like(b)))
+    torch.cuda.synchronize()
+    a, b, pa, pb = bufs[0]
+    assert ps.ps_prefix_pairs_static(a.data_ptr(), b.data_ptr(), pa.data_ptr(), pb.data_ptr(), 1) == ps.PS_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for (a, b, pa, pb), n in zip(bufs, sizes):
+            assert ps.ps_prefix_pairs_static(a.data_ptr(), b.data_ptr(), pa.data_ptr(),
+                                             pb.data_ptr(), n) == ps.PS_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    a, b, pa, pb = bufs[-1]
+    n = sizes[-1]
+    assert pa.cpu().numpy().tolist() == np.cumsum(np.arange(n)).tolist()
+    assert pb.cpu().numpy().tolist() == list(range(1, n + 1))
