@@ -338,13 +338,14 @@ def _run_cuda(args, g, wl, leg):
     assert n3 == k3 and nc == kc
     ps.load_library()
     chunk = args.order_chunk or min(max(k3, kc, 1), MAX_ORDER_CHUNK)
+    tuning = ps.make_tuning(adjacency=args.adjacency, hub_count=args.hub_count)
 
     stream = torch.cuda.Stream(device)
     sp = stream.cuda_stream
     with torch.cuda.stream(stream):
         d_off = torch.as_tensor(g.off).to(device)
         d_col = torch.as_tensor(g.col).to(device)
-        nb = ps.ps_graph_workspace_bytes(g.n, g.nnz)
+        nb = ps.ps_graph_workspace_bytes(g.n, g.nnz, tuning)
         ws = torch.empty(nb, dtype=torch.uint8, device=device)
         hist = torch.zeros(16, dtype=torch.int64, device=device)
         # scratch of the draw-ordered samplers: one chunk
@@ -359,7 +360,7 @@ def _run_cuda(args, g, wl, leg):
             e = ev[i]
             e[0].record(stream)
             rc, h = ps.ps_load_csr(g.n, g.nnz, d_off.data_ptr(), d_col.data_ptr(), ws.data_ptr(), nb,
-                                   None, sp)
+                                   tuning, sp)
             ps._check(rc, "ps_load_csr")
             rc, st = ps.ps_tau_prefix(h, sp)
             ps._check(rc, "ps_tau_prefix", (ps.PS_OK, ps.PS_NO_PATHS))
@@ -430,7 +431,7 @@ def _run_cuda(args, g, wl, leg):
     if not args.no_e2e:
         h_off = torch.as_tensor(g.off).pin_memory()
         h_col = torch.as_tensor(g.col).pin_memory()
-        nb2 = ps.ps_end_to_end_workspace_bytes(g.n, g.nnz) + osb  # + draw-order scratch
+        nb2 = ps.ps_end_to_end_workspace_bytes(g.n, g.nnz, tuning) + osb  # + draw-order scratch
         del ws
         ws2 = torch.empty(nb2, dtype=torch.uint8, device=device)
         times = []
@@ -439,7 +440,7 @@ def _run_cuda(args, g, wl, leg):
             torch.cuda.synchronize(device)
             t0 = time.perf_counter()
             rc, est, lo, hi, h6, h4e, st2 = ps.ps_count_motifs_host(
-                h_off, h_col, k3, kc, seed, 0.01, ws2.data_ptr(), nb2, None, sp)
+                h_off, h_col, k3, kc, seed, 0.01, ws2.data_ptr(), nb2, tuning, sp)
             t1 = time.perf_counter()
             ps._check(rc, "ps_count_motifs_host", (ps.PS_OK, ps.PS_NO_PATHS))
             if i >= args.warmup:
@@ -560,8 +561,13 @@ def run_batched(args):
     specs = batched_pool_specs()
     hosts = _gen_many(specs, lambda s: gg.rmat(s[0], s[1], seed=s[2]))
     t_gen = time.perf_counter() - t0
+    # hub-bitmap rows per graph-size bucket, tuned on each bucket's largest graph
+    tuner = B.Autotuner()
     t0 = time.perf_counter()
-    graphs = [ps.Graph(h.off, h.col, device=device) for h in hosts]
+    hub_choice = tuner.tune_hubs(hosts)
+    t_tune_hubs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    graphs = [ps.Graph(h.off, h.col, device=device, tuning=tuner.graph_tuning(h.m)) for h in hosts]
     gset = B.GraphSet(graphs)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t0
@@ -570,7 +576,6 @@ def run_batched(args):
     for r in reqs:
         r.first_id = rank << 40  # disjoint id ranges per rank
     samples = sum(r.k for r in reqs)
-    tuner = B.Autotuner()
     cfg = tuner.tune_launch(gset, reqs)
     runner = B.BatchRunner(gset, reqs, cfg)
     runner.capture()
@@ -630,7 +635,12 @@ def run_batched(args):
             "batched_vs_plain_eager": statistics.mean(t_plain) / statistics.mean(t_graph),
             "batched_vs_plain_graph": statistics.mean(t_plain_graph) / statistics.mean(t_graph),
             "histograms_equal_plain": exact,
-            "autotune": {"choice": vars(cfg), "trials": tuner.log},
+            "autotune": {"choice": {**vars(cfg),
+                                    "hub_rows_by_size_bucket": {
+                                        f"edges<2^{[17, 20, 99][b]}" if b < 2 else "edges>=2^20":
+                                            {"rows": rows, "min_degree": deg}
+                                        for b, (rows, deg) in sorted(hub_choice.items())}},
+                         "trials": tuner.log, "tune_hubs_s": t_tune_hubs},
             "generation_s": t_gen, "load_all_graphs_s": t_load,
             "gpu_launches": args.steps,  # one queue kernel per replayed step
             "gpu_launches_eager_timing": int(l_eager),
@@ -760,6 +770,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_oracle_protocol(args):
+    """The oracle's own timings on the host cores, for the record: its prepare
+    and each sampler timed separately, on one core and on all cores, median of
+    `--oracle-reps` runs.  Sampling on one core takes a bounded slice of each
+    sampler's ids (stated); nothing is extrapolated.  Prints one JSON line."""
+    import oracle as O
+    wl = workloads()[args.workload]
+    g = wl["make"]()
+    cores = max(1, O.max_threads())
+    reps = args.oracle_reps
+    prep = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        og = O.prepare(g.off, g.col)
+        prep.append(time.perf_counter() - t0)
+    out = {"workload": args.workload, "host_cores": cores, "repeats": reps,
+           "prepare_s_median": statistics.median(prep), "prepare_s": prep, "sampling": {}}
+    for label, th, k3, kc in (("one_core", 1, min(wl["k3"], 1 << 20), min(wl["kc"], 1 << 20)),
+                              ("all_cores", cores, wl["k3"], wl["kc"])):
+        t3, tc = [], []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            h6 = O.sample_3paths(og, k3, wl["seed"], 0, threads=th)
+            t3.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            h4 = O.sample_centered(og, kc, wl["seed"], 0, threads=th)
+            tc.append(time.perf_counter() - t0)
+        out["sampling"][label] = {
+            "threads": th, "k3": k3, "kc": kc, "s_3path_median": statistics.median(t3),
+            "s_centred_median": statistics.median(tc),
+            "3path_samples_per_s": k3 / statistics.median(t3),
+            "centred_samples_per_s": kc / statistics.median(tc),
+            "hist6": [int(x) for x in h6], "hist4": [int(x) for x in h4]}
+    print(json.dumps({"oracle_protocol": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -771,6 +817,14 @@ def main():
     ap.add_argument("--order-chunk", type=int, default=0,
                     help="samples per chunk of the draw-ordered samplers (0: all of a call's "
                          f"samples, up to {MAX_ORDER_CHUNK})")
+    ap.add_argument("--adjacency", type=int, default=0,
+                    help="adjacency test: 0 default (hash set), 1 hash set, 2 search + hub rows, "
+                         "3 per-vertex tables")
+    ap.add_argument("--hub-count", type=int, default=0, help="hub bitmap rows (0 default, -1 none)")
+    ap.add_argument("--oracle-protocol", action="store_true",
+                    help="time the oracle alone (prepare and samplers separately, one core and all "
+                         "cores) on --workload and print its JSON line")
+    ap.add_argument("--oracle-reps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="served64: number of requests")
@@ -778,7 +832,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.oracle_protocol:
+        run_oracle_protocol(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched512":
         run_batched(args)

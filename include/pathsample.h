@@ -58,7 +58,9 @@ typedef struct {
                                    bitmap row; default: up to 1024 rows within 256 MB
                                    (adjacency 2) or 128 MB (adjacency 1, where a lookup
                                    whose larger label is a hub reads its row); -1 = none   */
-    int32_t samples_per_thread; /* reserved (1)                                             */
+    int32_t samples_per_thread; /* samples each thread of the batched launch keeps in flight
+                                   per step of its loop: 1 (default) or 2; the other
+                                   samplers take one at a time                             */
     int32_t adjacency;          /* adjacency test: 1 = hash set of the edges (default),
                                    2 = search of the sorted smaller list + hub bitmaps,
                                    3 = a hash table per adjacency list                      */
@@ -66,7 +68,9 @@ typedef struct {
                                    samples by edge draw when the graph has >= 2^20 edges
                                    and the chunk >= 2^18 samples, else take them in id
                                    order; 1 = always sort; -1 = never                       */
-    int32_t reserved;
+    int32_t hub_min_degree;     /* smallest degree given a hub bitmap row (default 64; the
+                                   rows go to the top hub_count labels of at least this
+                                   degree)                                                   */
 } ps_tuning;
 
 /* Totals of one graph, filled by ps_tau_prefix. */

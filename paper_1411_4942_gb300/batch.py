@@ -6,9 +6,10 @@ run by ps_batch_sample_prepared: resident blocks take items from the queue
 and add each item's class counts to its request's histogram slot.  Because
 draws are keyed by (seed, sample id), every request's histogram equals the
 one the plain per-graph calls produce.  Launches can be captured in a CUDA
-graph and replayed.  The autotuner picks block size, samples per item,
-resident blocks per SM and the adjacency variant (with its hub-bitmap count)
-by timing candidates; results never depend on the choice.
+graph and replayed.  The autotuner picks the launch (block size, samples per
+thread, samples per item, resident blocks per SM) and, per graph-size bucket,
+the hub-bitmap rows (how many, and from which degree) by timing candidates;
+results never depend on the choice.
 """
 from __future__ import annotations
 
@@ -33,14 +34,26 @@ class Request:
     slot: int = -1      # histogram slot (6 uint64); assigned by plan_items when -1
 
 
+# graphs with at least this many edges can have their large requests taken
+# in draw order (their records and rows no longer stay in L2)
+ORDERED_MIN_EDGES = 1 << 20
+NEVER = 1 << 62
+
+
 @dataclasses.dataclass
 class LaunchConfig:
     block_size: int = 256
     chunk: int = 1 << 16
     blocks_per_sm: int = 0
+    samples_per_thread: int = 1
+    # requests of at least this many samples on graphs of >= ORDERED_MIN_EDGES
+    # edges run through the draw-ordered samplers inside the same step (same
+    # counts); the queue kernel takes the rest
+    ordered_min_k: int = NEVER
 
     def tuning(self) -> ps.PsTuning:
-        return ps.make_tuning(block_size=self.block_size, blocks_per_sm=self.blocks_per_sm)
+        return ps.make_tuning(block_size=self.block_size, blocks_per_sm=self.blocks_per_sm,
+                              samples_per_thread=self.samples_per_thread)
 
 
 class GraphSet:
@@ -99,7 +112,13 @@ class BatchRunner:
         import torch
         self.gset, self.cfg = gset, cfg
         self.stream = stream
-        items, self.slots = plan_items(requests, cfg.chunk)
+        requests = list(requests)
+        plan_items(requests, cfg.chunk)  # assigns slots
+        self.ordered = [r for r in requests if r.k >= cfg.ordered_min_k and
+                        int(gset.graphs[r.graph].stats.m) >= ORDERED_MIN_EDGES]
+        big = {id(r) for r in self.ordered}
+        items, self.slots = plan_items([r for r in requests if id(r) not in big], cfg.chunk)
+        self.slots = max([self.slots] + [r.slot + 1 for r in self.ordered])
         self.n_items = int(items.shape[0])
         dev = gset.device
         self.d_items = torch.from_numpy(items.view(np.uint8).copy()).to(dev)
@@ -107,15 +126,26 @@ class BatchRunner:
         self.d_counter = torch.zeros(2, dtype=torch.int32, device=dev)
         self.tuning = cfg.tuning()
         self.graph = None
+        # scratch of the draw-ordered calls: one chunk of the largest of them
+        self.d_order = None
+        if self.ordered:
+            k_max = min(max(r.k for r in self.ordered), 1 << 24)
+            self.d_order = torch.empty(ps.ps_ordered_scratch_bytes(k_max), dtype=torch.uint8, device=dev)
 
     def launch(self, zero: bool = True):
         if zero:
             self.d_hist.zero_()
-        rc = ps.ps_batch_sample_prepared(self.gset.table.data_ptr(), len(self.gset),
-                                         self.d_items.data_ptr(), self.n_items,
-                                         self.d_hist.data_ptr(), self.d_counter.data_ptr(),
-                                         self.tuning, self.stream)
-        ps._check(rc, "ps_batch_sample_prepared")
+        if self.n_items:
+            rc = ps.ps_batch_sample_prepared(self.gset.table.data_ptr(), len(self.gset),
+                                             self.d_items.data_ptr(), self.n_items,
+                                             self.d_hist.data_ptr(), self.d_counter.data_ptr(),
+                                             self.tuning, self.stream)
+            ps._check(rc, "ps_batch_sample_prepared")
+        for r in self.ordered:
+            fn = ps.ps_sample_3paths_ordered if r.sampler == SAMPLER_3PATH else ps.ps_sample_centered_ordered
+            rc = fn(self.gset.graphs[r.graph].handle, r.k, r.seed, r.first_id, self.d_hist.data_ptr() + 48 * r.slot,
+                    self.d_order.data_ptr(), self.d_order.numel(), self.stream)
+            ps._check(rc, "draw-ordered sample", (ps.PS_OK, ps.PS_NO_PATHS))
 
     def capture(self):
         """Record zeroing + the batched launch in a CUDA graph."""
@@ -191,12 +221,57 @@ class Autotuner:
     """Chooses launch parameters by timing candidates on (a slice of) the
     real batch; caches the choice per device and graph-size bucket."""
 
-    def __init__(self, block_sizes=(128, 256, 512), chunks=(1 << 14, 1 << 16, 1 << 18),
-                 blocks_per_sm=(0, 3)):
-        self.candidates = [LaunchConfig(b, c, p) for b, c, p in
-                           itertools.product(block_sizes, chunks, blocks_per_sm)]
+    # hub-bitmap settings tried per graph-size bucket: (rows, smallest degree);
+    # rows -1 = none
+    HUB_CHOICES = ((-1, 0), (256, 64), (1024, 64), (1024, 16))
+    # graph-size buckets by edges: below 2^17, below 2^20, the rest
+    SIZE_EDGES = (1 << 17, 1 << 20)
+    # smallest request taken in draw order (on graphs of >= ORDERED_MIN_EDGES)
+    ORDERED_MIN_K = (NEVER, 1 << 21, 1 << 19)
+
+    def __init__(self, block_sizes=(128, 256, 512), chunks=(1 << 12, 1 << 13, 1 << 14, 1 << 16, 1 << 18),
+                 blocks_per_sm=(0,), samples_per_thread=(1, 2)):
+        self.candidates = [LaunchConfig(b, c, p, t) for b, c, p, t in
+                           itertools.product(block_sizes, chunks, blocks_per_sm, samples_per_thread)]
         self.cache: dict = {}
+        self.hub_choice: dict = {}   # size bucket -> (rows, smallest degree)
         self.log: list = []
+
+    @classmethod
+    def size_bucket(cls, m: int) -> int:
+        return sum(m >= e for e in cls.SIZE_EDGES)
+
+    def graph_tuning(self, m: int) -> ps.PsTuning:
+        """The load-time tuning of a graph with m edges: its size bucket's hub
+        rows (the library's defaults before tune_hubs)."""
+        rows, deg = self.hub_choice.get(self.size_bucket(m), (0, 0))
+        return ps.make_tuning(hub_count=rows, hub_min_degree=deg)
+
+    def tune_hubs(self, hosts, k: int = 1 << 20, seed: int = 1):
+        """Hub rows per size bucket: the largest graph of each bucket is loaded
+        with every HUB_CHOICES setting and both samplers timed on it."""
+        reps = {}
+        for h in hosts:
+            b = self.size_bucket(h.m)
+            if b not in reps or h.m > reps[b].m:
+                reps[b] = h
+        for b, h in sorted(reps.items()):
+            best, best_ms = None, float("inf")
+            for rows, deg in self.HUB_CHOICES:
+                G = ps.Graph(h.off, h.col, tuning=ps.make_tuning(hub_count=rows, hub_min_degree=deg))
+
+                def both():
+                    hist = G.new_hist()
+                    G.sample_3paths(k, seed, 0, hist)
+                    G.sample_centered(k, seed, 0, hist)
+                ms = time_device(both, reps=2)
+                self.log.append({"size_bucket": b, "edges": int(h.m), "hub_rows": rows,
+                                 "hub_min_degree": deg, "hubs": int(G.stats.hubs), "ms": ms})
+                G.close()
+                if ms < best_ms:
+                    best, best_ms = (rows, deg), ms
+            self.hub_choice[b] = best
+        return dict(self.hub_choice)
 
     @staticmethod
     def bucket(gset: GraphSet) -> tuple:
@@ -220,8 +295,17 @@ class Autotuner:
             self.log.append({"cfg": dataclasses.asdict(cfg), "ms": ms})
             if ms < best_ms:
                 best, best_ms = cfg, ms
-        self.cache[key] = best
-        return best
+        # which requests go in draw order: timed on the whole batch
+        best_ms = float("inf")
+        for min_k in self.ORDERED_MIN_K:
+            cfg = dataclasses.replace(best, ordered_min_k=min_k)
+            runner = BatchRunner(gset, [dataclasses.replace(r) for r in requests], cfg)
+            ms = time_device(runner.launch, reps=2)
+            self.log.append({"cfg": dataclasses.asdict(cfg), "ms": ms, "whole_batch": True})
+            if ms < best_ms:
+                choice, best_ms = cfg, ms
+        self.cache[key] = choice
+        return choice
 
     def tune_graph_variant(self, off, col, k: int = 1 << 20, seed: int = 1,
                            hub_counts=(256, 1024)) -> ps.PsTuning:

@@ -83,6 +83,7 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
     r.blocks_per_sm = 0;
     r.guide_log2_ratio = 1;
     r.samples_per_thread = 1;
+    r.hub_min_degree = kHubMinDegree;
     r.adj_mode = kAdjHash;
     r.draw_order = 0;
     if (t && (t->adjacency == kAdjSearch || t->adjacency == kAdjVtab)) r.adj_mode = t->adjacency;
@@ -103,7 +104,8 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
         else if (t->guide_log2_ratio > 0) r.guide_log2_ratio = t->guide_log2_ratio > 4 ? 4 : t->guide_log2_ratio;
         if (t->hub_count < 0) r.hub_count = 0;
         else if (t->hub_count > 0) r.hub_count = t->hub_count;
-        if (t->samples_per_thread > 0) r.samples_per_thread = t->samples_per_thread;
+        if (t->samples_per_thread > 0) r.samples_per_thread = t->samples_per_thread >= 2 ? 2 : 1;
+        if (t->hub_min_degree > 0) r.hub_min_degree = t->hub_min_degree;
         r.draw_order = t->draw_order > 0 ? 1 : (t->draw_order < 0 ? -1 : 0);
     }
     if (r.hub_count > n) r.hub_count = static_cast<int>(n);
@@ -134,6 +136,7 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     if (n > scan_max) scan_max = n;
     if (l.m_cap > scan_max) scan_max = l.m_cap;
     if (l.gcap + 1 > scan_max) scan_max = l.gcap + 1;
+    if (256 * edge_sort_tiles(l.m_cap) > scan_max) scan_max = 256 * edge_sort_tiles(l.m_cap);
     l.scan_tiles = (scan_max + kScanTile - 1) / kScanTile + 1;
 
     const size_t n1 = static_cast<size_t>(n > 0 ? n : 1);
@@ -158,12 +161,12 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.hub = take(static_cast<size_t>(l.hub_cap) * l.hub_words * sizeof(uint32_t));
     l.eset = take(static_cast<size_t>(l.eset_buckets) * kBucketSlots * sizeof(uint64_t));
     l.vtab = take(static_cast<size_t>(l.vtab_slots) * sizeof(int32_t));
-    l.arcrow = take(static_cast<size_t>((nnz >> kArcRowShift) + 2) * sizeof(int32_t));
     l.keys0 = take(n1 * sizeof(uint32_t));
     l.keys1 = take(n1 * sizeof(uint32_t));
     l.vals0 = take(n1 * sizeof(uint32_t));
     l.vals1 = take(n1 * sizeof(uint32_t));
     l.rcounts = take(static_cast<size_t>(256) * l.radix_tiles * sizeof(uint32_t));
+    l.ecounts = take(static_cast<size_t>(256) * edge_sort_tiles(l.m_cap) * sizeof(uint32_t));
     l.scan_flag = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(uint32_t));
     l.scan_agg = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));
     l.scan_inc = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));
@@ -291,7 +294,6 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
     g->hub = reinterpret_cast<uint32_t *>(ws + L.hub);
     g->eset = L.eset_buckets ? reinterpret_cast<uint64_t *>(ws + L.eset) : nullptr;
     g->vtab = L.vtab_slots ? reinterpret_cast<int32_t *>(ws + L.vtab) : nullptr;
-    g->arcrow = reinterpret_cast<int32_t *>(ws + L.arcrow);
     const int rc = load_graph(g, d_off, d_col, reinterpret_cast<cudaStream_t>(stream));
     if (rc != PS_OK) {
         delete g;

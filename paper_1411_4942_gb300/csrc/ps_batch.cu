@@ -36,12 +36,46 @@ __device__ __forceinline__ int batch_sample(const GraphDev &g, int sampler, uint
     return sampler == 0 ? sample_3path<ADJ, false>(g, seed, id) : sample_centred<ADJ, false>(g, seed, id);
 }
 
+// Two samples of one thread with the hash-set adjacency, their steps
+// interleaved: both draws (edge, record, neighbours) as straight-line code,
+// then both samples' tests, so the two dependent chains overlap.  The same
+// counts as two calls of batch_sample.
+__device__ __forceinline__ void batch_sample2_hash(const GraphDev &g, int sampler, uint64_t seed, uint64_t id0,
+                                                   uint64_t id1, int &c0, int &c1) {
+    EdgeRec e0, e1;
+    int32_t a0, b0, a1, b1;
+    if (sampler == 0) {
+        path3_draw(g, seed, id0, e0, a0, b0);
+        path3_draw(g, seed, id1, e1, a1, b1);
+        bool x0, y0, z0, x1, y1, z1;
+        pair_test3<false>(g, a0, e0.v, e0.u, b0, a0, b0, x0, y0, z0);
+        pair_test3<false>(g, a1, e1.v, e1.u, b1, a1, b1, x1, y1, z1);
+        c0 = a0 == b0 ? 0 : class3(x0, y0, z0);
+        c1 = a1 == b1 ? 0 : class3(x1, y1, z1);
+    } else {
+        centred_draw(g, seed, id0, e0, a0, b0);
+        centred_draw(g, seed, id1, e1, a1, b1);
+        bool k0, k1;
+        eset_contains2(g.eset, g.eset_mask, a0, b0, a1, b1, k0, k1);
+        // the chords only for centred paths (the pair test also answers u' == v')
+        k0 = k0 && a0 != b0;
+        k1 = k1 && a1 != b1;
+        bool p0 = false, q0 = false, p1 = false, q1 = false;
+        if (k0) pair_test2<false>(g, e0.v, a0, e0.u, b0, p0, q0);
+        if (k1) pair_test2<false>(g, e1.v, a1, e1.u, b1, p1, q1);
+        c0 = k0 ? 1 + (int)p0 + (int)q0 : 0;
+        c1 = k1 ? 1 + (int)p1 + (int)q1 : 0;
+    }
+}
+
 // ADJ = 0: any variant, chosen per item; otherwise the table's only variant.
 // counter[0] hands out items; counter[1] counts items skipped because their
 // graph does not use the variant this kernel was compiled for.  Registers
-// are capped for 1024 resident threads per SM, the plain samplers' occupancy.
-template <int BLOCK, int ADJ>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
+// are capped for 1024 resident threads per SM with one sample per thread in
+// flight (SPT = 1), 512 with two (SPT = 2, hash-set graphs; other variants
+// take their two samples one after the other).
+template <int BLOCK, int ADJ, int SPT>
+__global__ void __launch_bounds__(BLOCK, (SPT == 1 ? 1024 : 512) / BLOCK)
 k_batch(const GraphDev *__restrict__ table, int32_t n_graphs, const ps_work *__restrict__ items,
         int64_t n_items, uint64_t *hist, uint32_t *counter) {
     __shared__ int64_t s_item;
@@ -71,7 +105,16 @@ k_batch(const GraphDev *__restrict__ table, int32_t n_graphs, const ps_work *__r
         cnt.zero();
         const int sampler = static_cast<int>(w.sampler);
         const bool any = sampler == 0 ? s_g.W > 0 : s_g.Lambda > 0;
-        if (any) {
+        if (any && SPT == 2 && (ADJ == kAdjHash || (ADJ == 0 && s_g.adj_mode == kAdjHash))) {
+            for (uint32_t s = threadIdx.x; s < w.count; s += 2 * BLOCK) {
+                // a lone last sample repeats its own id as the second, whose class is dropped
+                const uint32_t s1 = s + BLOCK < w.count ? s + BLOCK : s;
+                int c0, c1;
+                batch_sample2_hash(s_g, sampler, w.seed, w.first_id + s, w.first_id + s1, c0, c1);
+                cnt.add(c0);
+                if (s1 != s) cnt.add(c1);
+            }
+        } else if (any) {
             for (uint32_t s = threadIdx.x; s < w.count; s += BLOCK) {
                 if (ADJ != 0) {
                     cnt.add(batch_sample<ADJ>(s_g, sampler, w.seed, w.first_id + s));
@@ -87,22 +130,30 @@ k_batch(const GraphDev *__restrict__ table, int32_t n_graphs, const ps_work *__r
     }
 }
 
-template <int BLOCK, int ADJ>
+template <int BLOCK, int ADJ, int SPT>
 static int launch_batch_t(const void *d_table, int32_t n_graphs, const ps_work *d_items, int64_t n_items,
                           uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s) {
     int per_sm = t.blocks_per_sm;
     if (per_sm <= 0) {
         int occ = 0;
-        PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<BLOCK, ADJ>, BLOCK, 0));
+        PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<BLOCK, ADJ, SPT>, BLOCK, 0));
         per_sm = occ > 0 ? occ : 1;
     }
     int64_t blocks = (int64_t)sm_count_of_current_device() * per_sm;
     if (blocks > n_items) blocks = n_items;
     PS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, 2 * sizeof(uint32_t), s));
-    k_batch<BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(static_cast<const GraphDev *>(d_table), n_graphs,
-                                                           d_items, n_items, d_hist, d_counter);
+    k_batch<BLOCK, ADJ, SPT><<<(unsigned)blocks, BLOCK, 0, s>>>(static_cast<const GraphDev *>(d_table), n_graphs,
+                                                                d_items, n_items, d_hist, d_counter);
     PS_LAUNCH_CHECK();
     return PS_OK;
+}
+
+template <int BLOCK, int ADJ>
+static int launch_batch_s(const void *d_table, int32_t n_graphs, const ps_work *d_items, int64_t n_items,
+                          uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s) {
+    return t.samples_per_thread >= 2
+               ? launch_batch_t<BLOCK, ADJ, 2>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s)
+               : launch_batch_t<BLOCK, ADJ, 1>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
 }
 
 template <int BLOCK>
@@ -110,13 +161,13 @@ static int launch_batch_b(const void *d_table, int32_t n_graphs, const ps_work *
                           uint64_t *d_hist, uint32_t *d_counter, const Tuning &t, cudaStream_t s) {
     switch (table_adjacency(d_table)) {
         case kAdjHash:
-            return launch_batch_t<BLOCK, kAdjHash>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
+            return launch_batch_s<BLOCK, kAdjHash>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
         case kAdjSearch:
-            return launch_batch_t<BLOCK, kAdjSearch>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
+            return launch_batch_s<BLOCK, kAdjSearch>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
         case kAdjVtab:
-            return launch_batch_t<BLOCK, kAdjVtab>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
+            return launch_batch_s<BLOCK, kAdjVtab>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
         default:
-            return launch_batch_t<BLOCK, 0>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
+            return launch_batch_s<BLOCK, 0>(d_table, n_graphs, d_items, n_items, d_hist, d_counter, t, s);
     }
 }
 

@@ -55,6 +55,7 @@ enum {
     ST_N1_LO = 7, ST_N1_HI = 8,
     ST_HUBS = 9,
     ST_TIER = 10,      // 5 words: row boundaries of the sort tiers
+    ST_LONG = 15,      // first row longer than kLongRow (its arcs are walked by a block)
     ST_COUNTER = 16,   // 16 words: tile counters of scans (as uint32 pairs)
     ST_WORDS = 64
 };

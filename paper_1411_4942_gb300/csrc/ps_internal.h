@@ -16,9 +16,11 @@ namespace ps {
 constexpr int kTierA = 32;      // one warp, one key per lane
 constexpr int kTierB = 1024;    // one warp, up to 32 keys per lane in registers
 constexpr int kTierC = 4096;    // one block, registers + 16 KB shared; above: block radix sort
-// Arc-to-row index: the row holding every 2^kArcRowShift-th arc.
-constexpr int kArcRowShift = 8;
-// Hub rows are only worth a bitmap above this degree.
+// Rows longer than this have their arcs walked by a whole block (lower-arc
+// listing, hash set build); shorter rows by a warp per 32 rows.
+constexpr int kLongRow = 128;
+// Hub rows are only worth a bitmap above this degree (default of the tuning
+// field hub_min_degree).
 constexpr int kHubMinDegree = 64;
 // Items per tile of every scan.
 constexpr int kScanBlock = 256;
@@ -34,7 +36,8 @@ struct Tuning {
     int blocks_per_sm;
     int guide_log2_ratio;  // -1: no guide
     int hub_count;         // 0: none
-    int samples_per_thread;
+    int samples_per_thread;  // batched launch: 1 or 2
+    int hub_min_degree;
     int adj_mode;          // kAdjHash or kAdjSearch
     int draw_order;        // ordered samplers: 0 by size, 1 always, -1 never
 };
@@ -44,8 +47,8 @@ struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
     int64_t eset_buckets;  // 0 without the edge hash set
     int64_t vtab_slots;    // 0 without the per-vertex tables
-    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab, arcrow;
-    size_t keys0, keys1, vals0, vals1, rcounts, scan_flag, scan_agg, scan_inc;
+    size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab;
+    size_t keys0, keys1, vals0, vals1, rcounts, ecounts, scan_flag, scan_agg, scan_inc;
     size_t total;
 };
 bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L);
@@ -73,7 +76,6 @@ struct ps_graph {
     uint32_t *hub;
     uint64_t *eset;
     int32_t *vtab;
-    int32_t *arcrow;  // row of every kArcRowStep-th arc of the canonical CSR
     bool prefixed;
     ps_stats stats;
     ps::GraphDev dev;
@@ -137,6 +139,29 @@ k_radix_scatter(int64_t n, const uint32_t *__restrict__ kin, const uint32_t *__r
 template <typename T>
 ScanState<T> scan_state(ps_graph *g, int counter_slot);
 int reset_scan(ps_graph *g, int counter_slot, int64_t count, cudaStream_t s);
+
+// Scans `count` items of the graph's workspace through the shared scan
+// state (one scan at a time per graph, in stream order).
+template <typename T, typename Op, typename Load, typename Store>
+inline int run_scan(ps_graph *g, int slot, int64_t count, T identity, Op op, Load load, Store store,
+                    cudaStream_t s) {
+    if (count <= 0) return PS_OK;
+    int rc = reset_scan(g, slot, count, s);
+    if (rc) return rc;
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    k_scan<T, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
+        count, scan_state<T>(g, slot), identity, op, load, store);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
+// The edge table (ps_edges.cu): after the rows are relabelled and sorted and
+// ubase is known, writes every edge record, and raises F_ASYM for an
+// asymmetric input.
+int build_edge_table(ps_graph *g, cudaStream_t s);
+// Tiles of the edge table's radix sort for m edges (its digit counts take
+// 256 words per tile).
+int64_t edge_sort_tiles(int64_t m);
 
 // steps (one translation unit each)
 int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStream_t s);

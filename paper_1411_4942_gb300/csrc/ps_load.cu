@@ -33,19 +33,6 @@ int reset_scan(ps_graph *g, int counter_slot, int64_t count, cudaStream_t s) {
     return PS_OK;
 }
 
-template <typename T, typename Op, typename Load, typename Store>
-static int run_scan(ps_graph *g, int slot, int64_t count, T identity, Op op, Load load, Store store,
-                    cudaStream_t s) {
-    if (count <= 0) return PS_OK;
-    int rc = reset_scan(g, slot, count, s);
-    if (rc) return rc;
-    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
-    k_scan<T, kScanBlock, kScanItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
-        count, scan_state<T>(g, slot), identity, op, load, store);
-    PS_LAUNCH_CHECK();
-    return PS_OK;
-}
-
 // ------------------------------------------------------------------ degrees
 
 __global__ void k_degrees(int64_t n, int64_t nnz, const int64_t *__restrict__ off,
@@ -169,48 +156,21 @@ struct StoreOffsets {
     }
 };
 
-// arcrow[q] = the row holding arc q << kArcRowShift (every such arc lies in
-// exactly one non-empty row); arcrow[Q] = n - 1 closes the last interval.
-// Kernels that give each thread a run of arcs find its row between two
-// entries instead of searching all n offsets.
-__global__ void k_arc_rows(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, int32_t *arcrow) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t q_end = (nnz + (1ll << kArcRowShift) - 1) >> kArcRowShift;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        const int64_t a = coff[r], b = coff[r + 1];
-        for (int64_t q = (a + (1ll << kArcRowShift) - 1) >> kArcRowShift; (q << kArcRowShift) < b; q++)
-            arcrow[q] = static_cast<int32_t>(r);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) arcrow[q_end] = static_cast<int32_t>(n > 0 ? n - 1 : 0);
-}
-
-// Row of arc i (the last row r with coff[r] <= i), searched between the
-// arc-to-row entries around i.
-__device__ __forceinline__ int64_t row_of_arc(const int64_t *coff, const int32_t *arcrow, int64_t i) {
-    const int64_t q = i >> kArcRowShift;
-    int64_t lo = ldg_i32(arcrow + q), hi = ldg_i32(arcrow + q + 1);
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (ldg_i64(coff + mid) <= i) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // first row whose degree exceeds each tier limit (rows are degree-sorted)
 __global__ void k_tiers(int64_t n, const int32_t *__restrict__ dnew, u64 *status) {
-    const int lim[4] = {0, kTierA, kTierB, kTierC};
+    const int lim[5] = {0, kTierA, kTierB, kTierC, kLongRow};
+    const int slot[5] = {ST_TIER, ST_TIER + 1, ST_TIER + 2, ST_TIER + 3, ST_LONG};
     const int t = threadIdx.x;
-    if (t < 4) {
+    if (t < 5) {
         int64_t lo = 0, hi = n;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if (dnew[mid] > lim[t]) hi = mid;
             else lo = mid + 1;
         }
-        status[ST_TIER + t] = static_cast<u64>(lo);
+        status[slot[t]] = static_cast<u64>(lo);
     }
-    if (t == 4) status[ST_TIER + 4] = static_cast<u64>(n);
+    if (t == 5) status[ST_TIER + 4] = static_cast<u64>(n);
 }
 
 // ------------------------------------------------------- row relabel + sort
@@ -680,18 +640,6 @@ struct StoreUbase {
     }
 };
 
-// Edge j = (u, v), u < v, in row-major order: j = ubase[u] + (iu - lowcnt[u]).
-// Each lower arc (v -> u, at position jv of N(v)) finds v in the upper part
-// of N(u) and writes the whole 32-byte record of its edge: a full sector, so
-// the scattered writes cost no partial-sector traffic.  The upper part of
-// N(u) holds only neighbours of degree >= d_u, so it has at most sqrt(2m)
-// entries (the searches from the other side, in lower parts, are about 2^3.7
-// times longer on skewed graphs); the search halves it down to a window of
-// kEdgeWindow entries and then reads the whole window with independent loads
-// (one memory round trip instead of four dependent ones).  A lower arc
-// without its upper partner means an asymmetric input.
-constexpr int kEdgeItems = 8;
-constexpr int kEdgeWindow = 16;
 // Slots of a bucket are tried from the key's own first slot on, which spreads
 // the first attempts over the four slots (fewer failed compare-and-swaps than
 // always starting at slot 0).
@@ -711,81 +659,98 @@ __device__ __forceinline__ bool eset_insert(uint64_t *set, uint64_t mask, uint64
     return false;
 }
 
-// (Advancing four arcs' searches in step, and full occupancy at 32
-// registers, both measured slower.)
-__global__ void __launch_bounds__(256)
-k_edges(int64_t n, int64_t nnz, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
-        const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase,
-        const int32_t *__restrict__ arcrow, EdgeRec *rec, int64_t m_cap, u64 *status) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    bool asym = false;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c * kEdgeItems < nnz; c += stride) {
-        const int64_t i0 = c * kEdgeItems;
-        int64_t r = row_of_arc(coff, arcrow, i0);
-        int64_t ro = ldg_i64(coff + r);
-        int64_t rend = ldg_i64(coff + r + 1);
-        for (int t = 0; t < kEdgeItems; t++) {
-            const int64_t i = i0 + t;
-            if (i >= nnz) break;
-            while (rend <= i) {
-                r++;
-                ro = rend;
-                rend = ldg_i64(coff + r + 1);
-            }
-            const int32_t x = ldg_i32(ccol + i);
-            if (x >= r) continue;  // upper arcs are written from the other side
-            const int64_t ox = ldg_i64(coff + x);
-            const int32_t lx = ldg_i32(lowcnt + x);
-            const int64_t dx = ldg_i64(coff + x + 1) - ox;
-            // r sits in the upper part [a, b) of N(x) when the input is symmetric
-            int64_t a = ox + lx, b = ox + dx;
-            while (b - a > kEdgeWindow) {
-                const int64_t mid = a + ((b - a) >> 1);
-                if (ldg_i32(ccol + mid) <= r) a = mid;
-                else b = mid;
-            }
-            int below = 0;
-            bool hit = false;
+// Inserts every edge {r, x}, r < x, into the hash set with compare-and-swap:
+// the upper arcs of the sorted rows (row r's entries after its lowcnt[r]
+// lower ones) are exactly the edges, so the set needs neither the edge table
+// nor its order and is built as soon as the rows are sorted, on a side
+// stream beside the edge table.  The set's contents are deterministic, its
+// slot layout is not.  kInsertBatch keys per lane: their first
+// compare-and-swaps are issued together (most succeed at once), and only
+// the keys whose first slot was taken go on to the full insertion.
+constexpr int kInsertBatch = 4;
+#ifndef PS_ESET_BLOCKS
+#define PS_ESET_BLOCKS 8
+#endif
+// resident blocks per SM of the hash set build beside the edge table
+constexpr int kEsetBlocksPerSm = PS_ESET_BLOCKS;
+
+__device__ __forceinline__ bool eset_insert_batch(uint64_t *set, uint64_t mask, const uint64_t (&key)[kInsertBatch],
+                                                  const bool (&ok)[kInsertBatch]) {
+    unsigned long long old[kInsertBatch];
 #pragma unroll
-            for (int w = 0; w < kEdgeWindow; w++)
-                if (a + w < b) {
-                    const int32_t c = ldg_i32(ccol + a + w);
-                    below += c < r;
-                    hit |= c == r;
-                }
-            if (!hit) {
-                asym = true;
-                continue;
-            }
-            const int32_t iu = static_cast<int32_t>(a + below - ox);
-            const int64_t j = ldg_i64(ubase + x) + (iu - lx);
-            if (j < 0 || j >= m_cap) {
-                asym = true;
-                continue;
-            }
-            const int32_t dr = static_cast<int32_t>(rend - ro);
-            const int32_t p = static_cast<int32_t>(i - ro);
-            int4 *e = reinterpret_cast<int4 *>(rec + j);
-            e[0] = make_int4(x, static_cast<int32_t>(r), static_cast<int32_t>(dx), dr);
-            e[1] = make_int4(iu, p, static_cast<int32_t>(ox), static_cast<int32_t>(ro));
+    for (int u = 0; u < kInsertBatch; u++) {
+        old[u] = kEmptySlot;
+        if (ok[u]) {
+            const uint64_t h = key_hash(key[u]);
+            const int first = static_cast<int>(h >> (64 - kBucketShift));
+            unsigned long long *slot = reinterpret_cast<unsigned long long *>(set + ((h & mask) << kBucketShift));
+            old[u] = atomicCAS(slot + first, kEmptySlot, key[u]);
         }
     }
-    if (asym) raise_flag(status, F_ASYM);
+    bool good = true;
+#pragma unroll
+    for (int u = 0; u < kInsertBatch; u++)
+        if (ok[u] && old[u] != kEmptySlot && old[u] != key[u]) good &= eset_insert(set, mask, key[u]);
+    return good;
 }
 
-// Inserts every edge (u < v) of the edge table into the hash set with
-// compare-and-swap; the set's contents are deterministic, its slot layout is
-// not.  (A separate pass: inside the edge-table kernel the dependent CAS
-// chains stall threads that are already waiting on their searches, and
-// reading the keys from the sorted rows instead of the table's coalesced
-// (u, v) pairs measured 2.7x slower.)
+// The upper arcs in row-major order are the edges in edge order: edge
+// t = ubase[r] + q is the q-th upper arc of row r, at position
+// lowcnt[r] + q of N(r).  Each warp takes kEsetChunk consecutive edges (rows
+// are in degree order, so 32 consecutive rows can hold 32 sqrt(2m) edges:
+// the work is split by edges, not rows): it finds the row of its first edge
+// by a binary search of ubase, then walks windows of 32 rows, each lane
+// finding its edges' rows within the window by a shuffle search of their
+// ubase values, kInsertBatch * 32 edges at a time.
+constexpr int64_t kEsetChunk = 1024;
+
 __global__ void __launch_bounds__(256)
-k_eset_build(int64_t m, const EdgeRec *__restrict__ rec, uint64_t *set, uint64_t mask, u64 *status) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+k_eset_upper(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+             const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, uint64_t *set, uint64_t mask,
+             u64 *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
     bool failed = false;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const int2 uv = __ldg(reinterpret_cast<const int2 *>(rec + j));
-        failed |= !eset_insert(set, mask, edge_key(uv.x, uv.y));
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; c * kEsetChunk < m; c += nwarps) {
+        const int64_t t_lo = c * kEsetChunk, t_hi = (t_lo + kEsetChunk < m) ? t_lo + kEsetChunk : m;
+        // the row holding edge t_lo: the last r with ubase[r] <= t_lo
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (ldg_i64(ubase + mid) <= t_lo) lo = mid;
+            else hi = mid - 1;
+        }
+        // every window advances r0, so the walk ends by the last row even when
+        // an asymmetric input has fewer edges than the chunks cover
+        for (int64_t r0 = lo, t = t_lo; t < t_hi && r0 < n; r0 += 32) {
+            const int64_t r = r0 + lane;
+            int64_t ub = m, first = 0;  // lanes past the last row never match
+            if (r < n) {
+                ub = ldg_i64(ubase + r);
+                first = ldg_i64(coff + r) + ldg_i32(lowcnt + r);  // the row's first upper arc
+            }
+            const int64_t w_end = ldg_i64(ubase + (r0 + 32 < n ? r0 + 32 : n));
+            const int64_t seg_end = w_end < t_hi ? w_end : t_hi;
+            for (int64_t t0 = t; t0 < seg_end; t0 += 32 * kInsertBatch) {
+                uint64_t key[kInsertBatch];
+                bool ok[kInsertBatch];
+#pragma unroll
+                for (int u = 0; u < kInsertBatch; u++) {
+                    const int64_t tt = t0 + 32 * u + lane;
+                    int at = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int64_t x = __shfl_sync(0xffffffffu, ub, at + step);
+                        if (x <= tt) at += step;
+                    }
+                    const int64_t i = __shfl_sync(0xffffffffu, first, at) + (tt - __shfl_sync(0xffffffffu, ub, at));
+                    ok[u] = tt < seg_end;
+                    key[u] = ok[u] ? edge_key(static_cast<int32_t>(r0 + at), ldg_i32(ccol + i)) : 0ull;
+                }
+                failed |= !eset_insert_batch(set, mask, key, ok);
+            }
+            t = seg_end;
+        }
     }
     if (failed) raise_flag(status, F_OVERFLOW);
 }
@@ -884,10 +849,6 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     PS_CUDA_TRY(cudaMemsetAsync(g->off, 0, sizeof(int64_t), s));
     int rc = run_scan<int64_t>(g, 1, n, (int64_t)0, OpSum(), LoadDeg{g->dnew}, StoreOffsets{g->off, n}, s);
     if (rc) return rc;
-    if (n > 0) {
-        k_arc_rows<<<sms * 4, 256, 0, s>>>(n, nnz, g->off, g->arcrow);
-        PS_LAUNCH_CHECK();
-    }
     k_tiers<<<1, 32, 0, s>>>(n, g->dnew, g->status);
     PS_LAUNCH_CHECK();
 
@@ -929,22 +890,16 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         if (rc) return rc;
     }
 
-    // (4) the edge numbering and the edge table
+    // (4) the edge numbering: ubase[r] = the edges (upper arcs) of the rows before r
     PS_CUDA_TRY(cudaMemsetAsync(g->ubase, 0, sizeof(int64_t), s));
     rc = run_scan<int64_t>(g, 2, n, (int64_t)0, OpSum(), LoadUp{g->dnew, g->lowcnt},
                            StoreUbase{g->ubase, n, g->status}, s);
     if (rc) return rc;
-    if (nnz > 0) {
-        int64_t blocks = ((nnz + kEdgeItems - 1) / kEdgeItems + 255) / 256;
-        if (blocks > (int64_t)sms * 64) blocks = (int64_t)sms * 64;
-        k_edges<<<(unsigned)blocks, 256, 0, s>>>(n, nnz, g->off, g->col, g->lowcnt, g->ubase, g->arcrow,
-                                                 g->rec, L.m_cap, g->status);
-        PS_LAUNCH_CHECK();
-    }
 
-    // (5) the edge hash set.  Only sampling reads it, so it is built on a side
-    // stream and left running: the caller's stream goes on to the prefixes,
-    // which wait for it only before their final status read (wait_eset).
+    // (5) the edge hash set.  Only sampling reads it, and it needs only the
+    // sorted rows and the edge numbering, so it is built on a side stream
+    // from here on, beside the edge table and the prefix step; ps_tau_prefix
+    // waits for it before its end (wait_eset).
     if (nnz > 0 && g->eset) {
         cudaStream_t es = s;
         cudaStream_t side[2];
@@ -956,16 +911,20 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         g->eset_pending = true;
         const uint64_t eset_mask = static_cast<uint64_t>(L.eset_buckets - 1);
         PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * kBucketSlots * L.eset_buckets, es));
-        // four blocks per SM: room for the prefix step's kernels beside it
-        // (the full-width grid measured 0.08 ms slower on R-MAT 20, 0.9 ms on
-        // the 3M-vertex graph)
-        int64_t eb = (L.m_cap + 255) / 256;
-        if (eb > (int64_t)sms * 4) eb = (int64_t)sms * 4;
+        const int64_t m_cap = L.m_cap;
+        int64_t eb = ((m_cap + kEsetChunk - 1) / kEsetChunk + 7) / 8;  // a warp per chunk of edges
+        if (eb > (int64_t)sms * kEsetBlocksPerSm) eb = (int64_t)sms * kEsetBlocksPerSm;
         if (eb < 1) eb = 1;
-        k_eset_build<<<(unsigned)eb, 256, 0, es>>>(L.m_cap, g->rec, g->eset, eset_mask, g->status);
+        k_eset_upper<<<(unsigned)eb, 256, 0, es>>>(n, m_cap, g->off, g->col, g->lowcnt, g->ubase, g->eset,
+                                                  eset_mask, g->status);
         PS_LAUNCH_CHECK();
         PS_CUDA_TRY(cudaEventRecord(g->ev[3], es));
     }
+
+    // (6) the edge table
+    rc = build_edge_table(g, s);
+    if (rc) return rc;
+
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));
     const uint64_t m_upper = st[ST_M_UPPER];

@@ -208,6 +208,79 @@ k_sample_ordered(GraphDev g, uint64_t kk, uint64_t seed, uint64_t first_id, cons
     flush_counts<BLOCK>(cnt, SAMPLER == 0 ? 6 : 4, hist);
 }
 
+#ifndef PS_SPLIT
+#define PS_SPLIT 0
+#endif
+#ifndef PS_SPLIT_TAIL_MINB
+#define PS_SPLIT_TAIL_MINB 8
+#endif
+
+// The split samplers (hash-set adjacency).  Phase one takes every sorted
+// sample's draw up to its four vertices and writes them as one 16-byte tuple
+// (u', v, u, v') in sorted order (a 3-path draw with u' == v' is counted in
+// bin 0 here and written with u' = -1); phase two reads the tuples in order
+// and runs the adjacency tests.  The dependent chain of each phase is half
+// the whole sample's, and phase two needs few registers, so it keeps more
+// tests in flight per SM.
+template <int SAMPLER, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_draw_tuples(GraphDev g, uint64_t kk, uint64_t seed, uint64_t first_id, const uint32_t *__restrict__ ids,
+              int4 *__restrict__ tup, uint64_t *hist) {
+    uint32_t tri = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+    for (uint64_t p = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; p < kk; p += stride) {
+        const uint64_t id = first_id + __ldg(ids + p);
+        EdgeRec e;
+        int32_t up, vp;
+        if (SAMPLER == 0) {
+            path3_draw(g, seed, id, e, up, vp);
+            if (up == vp) {
+                tri++;
+                up = -1;
+            }
+        } else {
+            centred_draw(g, seed, id, e, up, vp);
+        }
+        tup[p] = make_int4(up, e.v, e.u, vp);
+    }
+    if (SAMPLER == 0) {
+        __shared__ unsigned long long s_tri;
+        if (threadIdx.x == 0) s_tri = 0;
+        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tri += __shfl_down_sync(0xffffffffu, tri, o);
+        if ((threadIdx.x & 31) == 0 && tri) atomicAdd(&s_tri, (unsigned long long)tri);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_tri) atomicAdd(reinterpret_cast<unsigned long long *>(hist), s_tri);
+    }
+}
+
+template <int SAMPLER, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, PS_SPLIT_TAIL_MINB * 256 / BLOCK)
+k_test_tuples(GraphDev g, uint64_t kk, const int4 *__restrict__ tup, uint64_t *hist) {
+    Counts6 cnt;
+    cnt.zero();
+    const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+    for (uint64_t p = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; p < kk; p += stride) {
+        const int4 t = __ldg(tup + p);
+        if (SAMPLER == 0) {
+            if (t.x < 0) continue;  // counted by the first phase
+            bool e1, e2, e3;
+            pair_test3<true>(g, t.x, t.y, t.z, t.w, t.x, t.w, e1, e2, e3);
+            cnt.add(class3(e1, e2, e3));
+        } else {
+            if (!pair_test(g, t.x, t.w)) {  // not centred (also u' == v')
+                cnt.add(0);
+                continue;
+            }
+            bool c1, c2;
+            pair_test2<true>(g, t.y, t.x, t.z, t.w, c1, c2);
+            cnt.add(1 + (int)c1 + (int)c2);
+        }
+    }
+    flush_counts<BLOCK>(cnt, SAMPLER == 0 ? 6 : 4, hist);
+}
+
 template <int SAMPLER, int BLOCK, int ADJ>
 static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *hist,
                      char *scratch, uint64_t chunk, cudaStream_t s) {
@@ -245,9 +318,24 @@ static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
             PS_LAUNCH_CHECK();
             k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, bkt, ids);
             PS_LAUNCH_CHECK();
-            k_sample_ordered<SAMPLER, BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id,
-                                                                                    ids, hist);
-            PS_LAUNCH_CHECK();
+            if (PS_SPLIT && ADJ == kAdjHash) {
+                int4 *tup = reinterpret_cast<int4 *>(
+                    (reinterpret_cast<uintptr_t>(bkt + chunk) + 15) & ~static_cast<uintptr_t>(15));
+                int occ_a = 0, occ_b = 0;
+                PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_draw_tuples<SAMPLER, BLOCK>, BLOCK, 0));
+                PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_test_tuples<SAMPLER, BLOCK>, BLOCK, 0));
+                uint64_t ba = (kk + BLOCK - 1) / BLOCK, bb = ba;
+                if (ba > (uint64_t)g->sm_count * (occ_a > 0 ? occ_a : 1)) ba = (uint64_t)g->sm_count * (occ_a > 0 ? occ_a : 1);
+                if (bb > (uint64_t)g->sm_count * (occ_b > 0 ? occ_b : 1)) bb = (uint64_t)g->sm_count * (occ_b > 0 ? occ_b : 1);
+                k_draw_tuples<SAMPLER, BLOCK><<<(unsigned)ba, BLOCK, 0, s>>>(g->dev, kk, seed, first_id, ids, tup, hist);
+                PS_LAUNCH_CHECK();
+                k_test_tuples<SAMPLER, BLOCK><<<(unsigned)bb, BLOCK, 0, s>>>(g->dev, kk, tup, hist);
+                PS_LAUNCH_CHECK();
+            } else {
+                k_sample_ordered<SAMPLER, BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id,
+                                                                                        ids, hist);
+                PS_LAUNCH_CHECK();
+            }
         }
         k -= kk;
         first_id += kk;
@@ -277,18 +365,20 @@ static int ordered_s(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
     }
 }
 
-// Bytes per sample of a chunk: its sorted id and its bucket.
-constexpr size_t kOrderPerSample = sizeof(uint32_t) + sizeof(uint8_t);
+// Bytes per sample of a chunk: its sorted id and its bucket (and, for the
+// split samplers, its 16-byte tuple, 16-byte aligned).
+constexpr size_t kOrderPerSample = sizeof(uint32_t) + sizeof(uint8_t) + (PS_SPLIT ? sizeof(int4) : 0);
+constexpr size_t kOrderSlack = PS_SPLIT ? 16 : 0;
 
 size_t ordered_scratch_bytes(uint64_t k_chunk) {
     if (k_chunk == 0 || k_chunk > kOrderMaxChunk) return 0;
-    return kOrderHeader + static_cast<size_t>(k_chunk) * kOrderPerSample;
+    return kOrderHeader + kOrderSlack + static_cast<size_t>(k_chunk) * kOrderPerSample;
 }
 
 int launch_ordered(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *d_hist,
                    void *d_scratch, size_t scratch_bytes, cudaStream_t s) {
     if (scratch_bytes < ordered_scratch_bytes(1)) return PS_ERR_WORKSPACE;
-    uint64_t chunk = (scratch_bytes - kOrderHeader) / kOrderPerSample;
+    uint64_t chunk = (scratch_bytes - kOrderHeader - kOrderSlack) / kOrderPerSample;
     if (chunk > kOrderMaxChunk) chunk = kOrderMaxChunk;
     if (g->tune.draw_order < 0 || (g->tune.draw_order == 0 && g->m < kOrderMinEdges))
         return launch_sampler(g, sampler, k, seed, first_id, d_hist, s);

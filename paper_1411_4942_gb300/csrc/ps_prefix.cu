@@ -40,9 +40,10 @@ struct StorePrefix {
 };
 
 // N_1 = sum_v C(d_v, 3) (128-bit) and the number of hub rows: the top
-// `hub_cap` labels whose degree is at least kHubMinDegree.
+// `hub_cap` labels whose degree is at least `hub_min` (labels are in degree
+// order, so these are the last rows).
 __global__ void __launch_bounds__(256)
-k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, u64 *status) {
+k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, int64_t hub_min, u64 *status) {
     uint64_t lo = 0, hi = 0;
     unsigned long long hubs = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -61,7 +62,7 @@ k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, u6
             add128(lo, hi, qlo);
             hi += qhi;
         }
-        if (r >= n - hub_cap && d >= static_cast<uint64_t>(kHubMinDegree)) hubs++;
+        if (r >= n - hub_cap && d >= static_cast<uint64_t>(hub_min)) hubs++;
     }
     warp_add128(lo, hi);
 #pragma unroll
@@ -218,7 +219,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         PS_LAUNCH_CHECK();
     }
     if (n > 0) {
-        k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->status);
+        k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->tune.hub_min_degree, g->status);
         PS_LAUNCH_CHECK();
     }
     uint64_t st[ST_WORDS];

@@ -11,17 +11,15 @@
 
 namespace ps {
 
-// Class of one Alg. 1 output: 0 = triangle (u' == v'), 1 = 3-path,
-// 2 = tailed triangle, 3 = 4-cycle, 4 = chordal 4-cycle, 5 = 4-clique.
-// HUB_ALL: every adjacency test of a sample may read a hub row (see
-// pair_test3); false for kernels short of registers.
-template <int ADJ, bool HUB_ALL = true>
-__device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, uint64_t id) {
+// Alg. 1 up to the induced subgraph: the edge e drawn with probability
+// tau_e / W and the two neighbours u' (of u, not v) and v' (of v, not u).
+__device__ __forceinline__ void path3_draw(const GraphDev &g, uint64_t seed, uint64_t id, EdgeRec &e, int32_t &up,
+                                           int32_t &vp) {
     const uint4 w = sample_block(seed, id, 0, 0);
     uint64_t r;
     if (!lemire64((static_cast<uint64_t>(w.y) << 32) | w.x, g.W, r)) r = draw_r_retry(seed, id, 0, g.W);
     const int64_t j = find_edge(g.ptau, g.gtau, g.tau_shift, r);
-    const EdgeRec e = ldg_rec(g.rec + j);
+    e = ldg_rec(g.rec + j);
     // u' uniform over N(u) \ {v}: a in [0, d_u - 1), the slot of v maps to the last entry
     const uint32_t su = static_cast<uint32_t>(e.du - 1), sv = static_cast<uint32_t>(e.dv - 1);
     uint32_t a, b;
@@ -29,8 +27,27 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     if (!lemire32(w.w, sv, b)) b = draw_small_retry(seed, id, 0, 3, sv);
     const int32_t pa = (a == static_cast<uint32_t>(e.iu)) ? e.du - 1 : static_cast<int32_t>(a);
     const int32_t pb = (b == static_cast<uint32_t>(e.jv)) ? e.dv - 1 : static_cast<int32_t>(b);
-    const int32_t up = ldg_i32(g.col + e.ou + pa);
-    const int32_t vp = ldg_i32(g.col + e.ov + pb);
+    up = ldg_i32(g.col + e.ou + pa);
+    vp = ldg_i32(g.col + e.ov + pb);
+}
+
+// Class of a 3-path u'-u-v-v' (u' != v') from its three other pairs
+// (u', v), (u, v'), (u', v'): 1 = 3-path, 2 = tailed triangle, 3 = 4-cycle,
+// 4 = chordal 4-cycle, 5 = 4-clique.
+__device__ __forceinline__ int class3(bool e1, bool e2, bool e3) {
+    const int s = (int)e1 + (int)e2 + (int)e3;
+    return s == 0 ? 1 : (s == 1 ? (e3 ? 3 : 2) : (s == 2 ? 4 : 5));
+}
+
+// Class of one Alg. 1 output: 0 = triangle (u' == v'), 1 = 3-path,
+// 2 = tailed triangle, 3 = 4-cycle, 4 = chordal 4-cycle, 5 = 4-clique.
+// HUB_ALL: every adjacency test of a sample may read a hub row (see
+// pair_test3); false for kernels short of registers.
+template <int ADJ, bool HUB_ALL = true>
+__device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, uint64_t id) {
+    EdgeRec e;
+    int32_t up, vp;
+    path3_draw(g, seed, id, e, up, vp);
     if (up == vp) return 0;
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
     bool e1, e2, e3;
@@ -55,8 +72,27 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
         e2 = (e.u < vp) ? adjacent_known(g, e.u, e.ou, e.du, vp) : adjacent(g, vp, e.u);
         e3 = adjacent(g, up, vp);
     }
-    const int s = (int)e1 + (int)e2 + (int)e3;
-    return s == 0 ? 1 : (s == 1 ? (e3 ? 3 : 2) : (s == 2 ? 4 : 5));
+    return class3(e1, e2, e3);
+}
+
+// Alg. 3 up to the induced subgraph: the edge e drawn with probability
+// lambda_e / Lambda, u' among the L_{u,v} entries of N(u) after v and v'
+// among the L_{v,u} entries of N(v) after u.
+__device__ __forceinline__ void centred_draw(const GraphDev &g, uint64_t seed, uint64_t id, EdgeRec &e, int32_t &up,
+                                             int32_t &vp) {
+    const uint4 w = sample_block(seed, id, 0, 1);
+    uint64_t r;
+    if (!lemire64((static_cast<uint64_t>(w.y) << 32) | w.x, g.Lambda, r))
+        r = draw_r_retry(seed, id, 1, g.Lambda);
+    const int64_t j = find_edge(g.plam, g.glam, g.lam_shift, r);
+    e = ldg_rec(g.rec + j);
+    const uint32_t lu = static_cast<uint32_t>(e.du - 1 - e.iu);
+    const uint32_t lv = static_cast<uint32_t>(e.dv - 1 - e.jv);
+    uint32_t a, b;
+    if (!lemire32(w.z, lu, a)) a = draw_small_retry(seed, id, 1, 2, lu);
+    if (!lemire32(w.w, lv, b)) b = draw_small_retry(seed, id, 1, 3, lv);
+    up = ldg_i32(g.col + e.ou + e.iu + 1 + static_cast<int32_t>(a));
+    vp = ldg_i32(g.col + e.ov + e.jv + 1 + static_cast<int32_t>(b));
 }
 
 // Class of one Alg. 3 output: 0 = not centred, 1 = 4-cycle, 2 = chordal
@@ -65,19 +101,9 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
 // (Definition 4.1) iff (u', v') is an edge.
 template <int ADJ, bool HUB_ALL = true>
 __device__ __forceinline__ int sample_centred(const GraphDev &g, uint64_t seed, uint64_t id) {
-    const uint4 w = sample_block(seed, id, 0, 1);
-    uint64_t r;
-    if (!lemire64((static_cast<uint64_t>(w.y) << 32) | w.x, g.Lambda, r))
-        r = draw_r_retry(seed, id, 1, g.Lambda);
-    const int64_t j = find_edge(g.plam, g.glam, g.lam_shift, r);
-    const EdgeRec e = ldg_rec(g.rec + j);
-    const uint32_t lu = static_cast<uint32_t>(e.du - 1 - e.iu);
-    const uint32_t lv = static_cast<uint32_t>(e.dv - 1 - e.jv);
-    uint32_t a, b;
-    if (!lemire32(w.z, lu, a)) a = draw_small_retry(seed, id, 1, 2, lu);
-    if (!lemire32(w.w, lv, b)) b = draw_small_retry(seed, id, 1, 3, lv);
-    const int32_t up = ldg_i32(g.col + e.ou + e.iu + 1 + static_cast<int32_t>(a));
-    const int32_t vp = ldg_i32(g.col + e.ov + e.jv + 1 + static_cast<int32_t>(b));
+    EdgeRec e;
+    int32_t up, vp;
+    centred_draw(g, seed, id, e, up, vp);
     if (ADJ == kAdjVtab) {
         if (up == vp) return 0;
         // the chords (u', v) and (u, v') in the tables of v and u (rows known

@@ -40,7 +40,8 @@ def test_batched_equals_plain(graph_set):
     reqs = B.random_requests(rs, len(graph_set), log2_k=(10, 17))
     want = _plain(graph_set, reqs)
     for cfg in (B.LaunchConfig(256, 1 << 16, 0), B.LaunchConfig(128, 777, 3),
-                B.LaunchConfig(512, 1 << 12, 1)):
+                B.LaunchConfig(512, 1 << 12, 1), B.LaunchConfig(256, 1 << 13, 0, 2),
+                B.LaunchConfig(128, 999, 0, 2)):
         run = B.BatchRunner(graph_set, [B.Request(**vars(r)) for r in reqs], cfg)
         run.launch()
         torch.cuda.synchronize()
@@ -60,11 +61,14 @@ def test_cuda_graph_replay(graph_set):
 
 
 def test_autotuner_choice_keeps_results(graph_set):
+    import dataclasses
     rs = np.random.default_rng(9)
     reqs = B.random_requests(rs, len(graph_set), log2_k=(12, 15))
     tuner = B.Autotuner(block_sizes=(128, 256), chunks=(1 << 12, 1 << 15), blocks_per_sm=(0,))
     cfg = tuner.tune_launch(graph_set, reqs, budget_samples=1 << 18)
-    assert cfg in tuner.candidates and len(tuner.log) == len(tuner.candidates)
+    assert dataclasses.replace(cfg, ordered_min_k=B.NEVER) in tuner.candidates
+    assert {c.samples_per_thread for c in tuner.candidates} == {1, 2}
+    assert len(tuner.log) == len(tuner.candidates) + len(B.Autotuner.ORDERED_MIN_K)
     run = B.BatchRunner(graph_set, reqs, cfg)
     run.launch()
     torch.cuda.synchronize()
@@ -72,6 +76,16 @@ def test_autotuner_choice_keeps_results(graph_set):
     g = gg.rmat(11, 16.0, seed=3)
     t = tuner.tune_graph_variant(g.off, g.col, k=1 << 16)
     assert int(t.adjacency) in (ps.ADJ_HASH, ps.ADJ_SEARCH, ps.ADJ_VTAB)
+    # hub rows per size bucket; the chosen load-time tuning keeps every count
+    hosts = [gg.rmat(10, 8.0, seed=41), gg.rmat(14, 16.0, seed=42)]
+    choice = tuner.tune_hubs(hosts, k=1 << 15)
+    assert set(choice) == {B.Autotuner.size_bucket(h.m) for h in hosts}
+    assert all(c in B.Autotuner.HUB_CHOICES for c in choice.values())
+    for h in hosts:
+        G = ps.Graph(h.off, h.col, tuning=tuner.graph_tuning(h.m))
+        og = O.prepare(h.off, h.col)
+        got = G.sample_3paths(1 << 14, 5).cpu().numpy()[:6].astype(np.uint64)
+        assert got.tolist() == O.sample_3paths(og, 1 << 14, 5).tolist()
 
 
 def _sources(n_graphs):
@@ -131,14 +145,18 @@ def test_batched_slots_equal_oracle():
     for i, r in enumerate(reqs):
         if i % 3 == 1:
             r.first_id = (1 << 32) - 1000 + i
-    run = B.BatchRunner(gset, reqs, B.LaunchConfig(256, 1 << 12, 0))
-    run.launch()
-    torch.cuda.synchronize()
-    got = run.histograms()
     ogs = [O.prepare(h.off, h.col) for h in hosts]
-    for r in reqs:
-        want = _oracle_hist(ogs[r.graph], r.sampler, r.k, r.seed, r.first_id)
-        assert got[r.slot].tolist() == want.tolist(), (r, got[r.slot], want)
+    # one sample per thread; two per thread with the large graph's requests
+    # taken by the draw-ordered samplers
+    for cfg in (B.LaunchConfig(256, 1 << 12, 0), B.LaunchConfig(256, 1 << 12, 0, 2, ordered_min_k=1 << 10)):
+        run = B.BatchRunner(gset, reqs, cfg)
+        assert bool(run.ordered) == (cfg.ordered_min_k < B.NEVER)
+        run.launch()
+        torch.cuda.synchronize()
+        got = run.histograms()
+        for r in reqs:
+            want = _oracle_hist(ogs[r.graph], r.sampler, r.k, r.seed, r.first_id)
+            assert got[r.slot].tolist() == want.tolist(), (cfg, r, got[r.slot], want)
 
 
 @pytest.mark.parametrize("realtime", [True, False])
