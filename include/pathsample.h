@@ -54,10 +54,11 @@ typedef struct {
     int32_t block_size;         /* sampling threads per block: 128, 256 (default), 512, 1024 */
     int32_t blocks_per_sm;      /* resident sampling blocks per SM (default: occupancy)      */
     int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1); -1 = none  */
-    int32_t hub_count;          /* top-degree vertices (degree >= 64) given an adjacency
-                                   bitmap row; default: up to 1024 rows within 256 MB
-                                   (adjacency 2) or 128 MB (adjacency 1, where a lookup
-                                   whose larger label is a hub reads its row); -1 = none   */
+    int32_t hub_count;          /* top-degree vertices (degree >= hub_min_degree) given an
+                                   adjacency bitmap row; default: up to 1024 rows within
+                                   256 MB (adjacency 2) or 512 MB (adjacency 1, where a
+                                   lookup whose larger label is a hub reads its row);
+                                   -1 = none                                                */
     int32_t samples_per_thread; /* samples each thread of the batched launch keeps in flight
                                    per step of its loop: 1 (default) or 2; the other
                                    samplers take one at a time                             */

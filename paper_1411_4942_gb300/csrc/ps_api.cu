@@ -88,11 +88,13 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
     r.draw_order = 0;
     if (t && (t->adjacency == kAdjSearch || t->adjacency == kAdjVtab)) r.adj_mode = t->adjacency;
     // hub bitmap rows: up to 1024 within 256 MB for the search variant, which
-    // needs them for every hub pair; up to 1024 within 128 MB beside the hash
+    // needs them for every hub pair; up to 1024 within 512 MB beside the hash
     // set, where they answer the lookups naming a hub (on R-MAT 20: samplers
-    // 1.79 / 1.51 -> 1.65 / 1.29 ms, -3.4% on the whole step with their build)
+    // 1.79 / 1.51 -> 1.65 / 1.29 ms, -3.4% on the whole step with their build;
+    // on the 3M-vertex graph, whose rows are 375 KB, 3-path sampling 17.13 /
+    // 16.89 / 16.08 / 15.06 / 14.81 ms with 0 / 64 / 341 / 682 / 1024 rows)
     const int64_t row_bytes = ((n + 31) / 32) * 4;
-    const int64_t budget = (r.adj_mode == kAdjSearch ? 256ll : r.adj_mode == kAdjHash ? 128ll : 0ll) << 20;
+    const int64_t budget = (r.adj_mode == kAdjSearch ? 256ll : r.adj_mode == kAdjHash ? 512ll : 0ll) << 20;
     int64_t hubs = row_bytes > 0 ? budget / row_bytes : 0;
     if (hubs > 1024) hubs = 1024;
     r.hub_count = static_cast<int>(hubs);
@@ -106,7 +108,7 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
         else if (t->hub_count > 0) r.hub_count = t->hub_count;
         if (t->samples_per_thread > 0) r.samples_per_thread = t->samples_per_thread >= 2 ? 2 : 1;
         if (t->hub_min_degree > 0) r.hub_min_degree = t->hub_min_degree;
-        r.draw_order = t->draw_order > 0 ? 1 : (t->draw_order < 0 ? -1 : 0);
+        r.draw_order = t->draw_order >= 2 ? 2 : (t->draw_order > 0 ? 1 : (t->draw_order < 0 ? -1 : 0));
     }
     if (r.hub_count > n) r.hub_count = static_cast<int>(n);
     return r;
@@ -129,6 +131,7 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
         while (slots < 2 * l.m_cap) slots <<= 1;
         l.eset_buckets = slots / kBucketSlots;
     }
+    l.eset_regions = l.eset_buckets >= kRegionBuckets ? l.eset_buckets / kRegionBuckets : 0;
     l.vtab_slots = t.adj_mode == kAdjVtab ? 2 * nnz : 0;
     l.radix_tiles = (n + kRadixTile - 1) / kRadixTile;
     if (l.radix_tiles < 1) l.radix_tiles = 1;
@@ -167,6 +170,9 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.vals1 = take(n1 * sizeof(uint32_t));
     l.rcounts = take(static_cast<size_t>(256) * l.radix_tiles * sizeof(uint32_t));
     l.ecounts = take(static_cast<size_t>(256) * edge_sort_tiles(l.m_cap) * sizeof(uint32_t));
+    // the region build's key list and its per-region counts, offsets and cursors
+    l.ekeys = take(l.eset_regions ? static_cast<size_t>(l.m_cap) * sizeof(uint64_t) : 0);
+    l.eregion = take(l.eset_regions ? static_cast<size_t>(3 * (l.eset_regions + 1)) * sizeof(uint32_t) : 0);
     l.scan_flag = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(uint32_t));
     l.scan_agg = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));
     l.scan_inc = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));

@@ -409,10 +409,18 @@ __device__ __forceinline__ uint64_t l2_keep_policy() {
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+#ifndef PS_HUB_HINT
+#define PS_HUB_HINT 1
+#endif
 __device__ __forceinline__ uint32_t ld_hub_word(const uint32_t *p, uint64_t pol) {
+#if PS_HUB_HINT
     uint32_t v;
     asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
+#else
+    (void)pol;
+    return __ldg(p);
+#endif
 }
 
 // Address of the hub-row word holding bit a of hub c's row.

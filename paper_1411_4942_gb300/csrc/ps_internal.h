@@ -16,6 +16,9 @@ namespace ps {
 constexpr int kTierA = 32;      // one warp, one key per lane
 constexpr int kTierB = 1024;    // one warp, up to 32 keys per lane in registers
 constexpr int kTierC = 4096;    // one block, registers + 16 KB shared; above: block radix sort
+// The edge hash set is built region by region in shared memory (64 KB of
+// buckets each) once the table holds at least one whole region.
+constexpr int64_t kRegionBuckets = 2048;
 // Rows longer than this have their arcs walked by a whole block (lower-arc
 // listing, hash set build); shorter rows by a warp per 32 rows.
 constexpr int kLongRow = 128;
@@ -46,9 +49,10 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n);
 struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
     int64_t eset_buckets;  // 0 without the edge hash set
+    int64_t eset_regions;  // regions of the region build (0: the direct build)
     int64_t vtab_slots;    // 0 without the per-vertex tables
     size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab;
-    size_t keys0, keys1, vals0, vals1, rcounts, ecounts, scan_flag, scan_agg, scan_inc;
+    size_t keys0, keys1, vals0, vals1, rcounts, ecounts, ekeys, eregion, scan_flag, scan_agg, scan_inc;
     size_t total;
 };
 bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L);

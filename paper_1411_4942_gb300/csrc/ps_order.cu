@@ -52,10 +52,13 @@ __device__ __forceinline__ uint64_t draw_r_of(uint64_t total, uint64_t seed, uin
 // Bucket of every id of block b's run [b * per, (b + 1) * per) into bkt, and
 // the run's bucket counts into hist[bucket * kOrderMaxRuns + b] (per-warp
 // counters first).  Two draws per iteration, so two Philox chains overlap.
+// With `high` set (the two-pass order), r >> shift is a 16-bit range: its low
+// byte is the bucket of this pass and its high byte is stored in high[] for
+// the second pass.
 template <int SAMPLER>
 __global__ void __launch_bounds__(kOrderThreads)
 k_order_count(uint64_t total, uint64_t kk, uint64_t seed, uint64_t first_id, int shift, uint64_t per,
-              uint32_t *hist, uint8_t *bkt) {
+              uint32_t *hist, uint8_t *bkt, uint8_t *high) {
     __shared__ uint32_t s_h[kOrderWarps][kOrderBuckets];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kOrderWarps * kOrderBuckets; i += kOrderThreads) (&s_h[0][0])[i] = 0;
@@ -64,8 +67,14 @@ k_order_count(uint64_t total, uint64_t kk, uint64_t seed, uint64_t first_id, int
     const uint64_t hi = lo + per < kk ? lo + per : kk;
     for (uint64_t s = lo + threadIdx.x; s < hi; s += 2 * kOrderThreads) {
         const uint64_t s2 = s + kOrderThreads;
-        const uint32_t c = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s) >> shift);
-        const uint32_t c2 = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s2) >> shift);
+        uint32_t c = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s) >> shift);
+        uint32_t c2 = static_cast<uint32_t>(draw_r_of<SAMPLER>(total, seed, first_id + s2) >> shift);
+        if (high) {
+            high[s] = static_cast<uint8_t>(c >> 8);
+            if (s2 < hi) high[s2] = static_cast<uint8_t>(c2 >> 8);
+            c &= 255u;
+            c2 &= 255u;
+        }
         bkt[s] = static_cast<uint8_t>(c);
         atomicAdd(&s_h[warp][c], 1u);
         if (s2 < hi) {
@@ -73,6 +82,26 @@ k_order_count(uint64_t total, uint64_t kk, uint64_t seed, uint64_t first_id, int
             atomicAdd(&s_h[warp][c2], 1u);
         }
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kOrderWarps; w++) c += s_h[w][b];
+        hist[(size_t)b * kOrderMaxRuns + blockIdx.x] = c;
+    }
+}
+
+// The second pass's counts: the bucket of every position is the stored high
+// byte; per-run counts as in k_order_count.
+__global__ void __launch_bounds__(kOrderThreads)
+k_order_count_bytes(uint64_t kk, uint64_t per, const uint8_t *__restrict__ bkt, uint32_t *hist) {
+    __shared__ uint32_t s_h[kOrderWarps][kOrderBuckets];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kOrderWarps * kOrderBuckets; i += kOrderThreads) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)blockIdx.x * per;
+    const uint64_t hi = lo + per < kk ? lo + per : kk;
+    for (uint64_t s = lo + threadIdx.x; s < hi; s += kOrderThreads) atomicAdd(&s_h[warp][bkt[s]], 1u);
     __syncthreads();
     for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) {
         uint32_t c = 0;
@@ -135,14 +164,19 @@ k_order_offsets(int runs, uint32_t *hist, uint32_t *totals) {
 // written as one contiguous piece at the run's cursor for that bucket
 // (base[bucket] + the run's offset within it, advanced after every tile), so
 // the stores coalesce.  The buckets of the next tile are loaded while the
-// current one is placed.
+// current one is placed.  The value placed for input position q is q, or
+// vals[q] when vals is given (the second pass of the two-pass order, whose
+// input is the first pass's output); a byte carry[q] travels with it into
+// carry_out when carry is given.
 __global__ void __launch_bounds__(kOrderThreads)
 k_order_scatter(uint64_t kk, uint64_t per, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals,
-                const uint8_t *__restrict__ bkt, uint32_t *ids) {
+                const uint8_t *__restrict__ bkt, const uint32_t *__restrict__ vals, const uint8_t *__restrict__ carry,
+                uint32_t *__restrict__ ids, uint8_t *__restrict__ carry_out) {
     __shared__ uint32_t s_cur[kOrderBuckets], s_cnt[kOrderBuckets], s_off[kOrderBuckets];
     __shared__ uint32_t s_warp[kOrderBuckets / 32];
     __shared__ uint32_t s_id[kOrderTile];
     __shared__ uint8_t s_b[kOrderTile];
+    __shared__ uint8_t s_c[kOrderTile];
     const int t = threadIdx.x;
     {
         // the buckets' first positions: exclusive prefix of their totals
@@ -180,14 +214,18 @@ k_order_scatter(uint64_t kk, uint64_t per, const uint32_t *__restrict__ hist, co
         for (int i = 0; i < kOrderItems; i++) {
             if (myb[i] < kOrderBuckets) {
                 const uint32_t p = s_off[myb[i]] + rank[i];
-                s_id[p] = static_cast<uint32_t>(t0 + (uint64_t)i * kOrderThreads + t);
+                const uint64_t q = t0 + (uint64_t)i * kOrderThreads + t;
+                s_id[p] = vals ? vals[q] : static_cast<uint32_t>(q);
                 s_b[p] = static_cast<uint8_t>(myb[i]);
+                if (carry) s_c[p] = carry[q];
             }
         }
         __syncthreads();
         for (uint32_t p = t; p < all; p += kOrderThreads) {
             const uint32_t b = s_b[p];
-            ids[s_cur[b] + (p - s_off[b])] = s_id[p];
+            const uint32_t dst = s_cur[b] + (p - s_off[b]);
+            ids[dst] = s_id[p];
+            if (carry) carry_out[dst] = s_c[p];
         }
         __syncthreads();
         if (t < kOrderBuckets) s_cur[t] += s_cnt[t];
@@ -208,89 +246,24 @@ k_sample_ordered(GraphDev g, uint64_t kk, uint64_t seed, uint64_t first_id, cons
     flush_counts<BLOCK>(cnt, SAMPLER == 0 ? 6 : 4, hist);
 }
 
-#ifndef PS_SPLIT
-#define PS_SPLIT 0
-#endif
-#ifndef PS_SPLIT_TAIL_MINB
-#define PS_SPLIT_TAIL_MINB 8
-#endif
-
-// The split samplers (hash-set adjacency).  Phase one takes every sorted
-// sample's draw up to its four vertices and writes them as one 16-byte tuple
-// (u', v, u, v') in sorted order (a 3-path draw with u' == v' is counted in
-// bin 0 here and written with u' = -1); phase two reads the tuples in order
-// and runs the adjacency tests.  The dependent chain of each phase is half
-// the whole sample's, and phase two needs few registers, so it keeps more
-// tests in flight per SM.
-template <int SAMPLER, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_draw_tuples(GraphDev g, uint64_t kk, uint64_t seed, uint64_t first_id, const uint32_t *__restrict__ ids,
-              int4 *__restrict__ tup, uint64_t *hist) {
-    uint32_t tri = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
-    for (uint64_t p = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; p < kk; p += stride) {
-        const uint64_t id = first_id + __ldg(ids + p);
-        EdgeRec e;
-        int32_t up, vp;
-        if (SAMPLER == 0) {
-            path3_draw(g, seed, id, e, up, vp);
-            if (up == vp) {
-                tri++;
-                up = -1;
-            }
-        } else {
-            centred_draw(g, seed, id, e, up, vp);
-        }
-        tup[p] = make_int4(up, e.v, e.u, vp);
-    }
-    if (SAMPLER == 0) {
-        __shared__ unsigned long long s_tri;
-        if (threadIdx.x == 0) s_tri = 0;
-        __syncthreads();
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tri += __shfl_down_sync(0xffffffffu, tri, o);
-        if ((threadIdx.x & 31) == 0 && tri) atomicAdd(&s_tri, (unsigned long long)tri);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_tri) atomicAdd(reinterpret_cast<unsigned long long *>(hist), s_tri);
-    }
-}
-
-template <int SAMPLER, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, PS_SPLIT_TAIL_MINB * 256 / BLOCK)
-k_test_tuples(GraphDev g, uint64_t kk, const int4 *__restrict__ tup, uint64_t *hist) {
-    Counts6 cnt;
-    cnt.zero();
-    const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
-    for (uint64_t p = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; p < kk; p += stride) {
-        const int4 t = __ldg(tup + p);
-        if (SAMPLER == 0) {
-            if (t.x < 0) continue;  // counted by the first phase
-            bool e1, e2, e3;
-            pair_test3<true>(g, t.x, t.y, t.z, t.w, t.x, t.w, e1, e2, e3);
-            cnt.add(class3(e1, e2, e3));
-        } else {
-            if (!pair_test(g, t.x, t.w)) {  // not centred (also u' == v')
-                cnt.add(0);
-                continue;
-            }
-            bool c1, c2;
-            pair_test2<true>(g, t.y, t.x, t.z, t.w, c1, c2);
-            cnt.add(1 + (int)c1 + (int)c2);
-        }
-    }
-    flush_counts<BLOCK>(cnt, SAMPLER == 0 ? 6 : 4, hist);
-}
-
 template <int SAMPLER, int BLOCK, int ADJ>
 static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *hist,
                      char *scratch, uint64_t chunk, cudaStream_t s) {
     const uint64_t total = SAMPLER == 0 ? g->stats.W : g->stats.Lambda;
+    // the two-pass order sorts by 16 bits of r (65536 ranges), the one-pass by 8
+    const bool two_pass = g->tune.draw_order == 2;
+    const uint64_t ranges = two_pass ? 65536u : static_cast<uint64_t>(kOrderBuckets);
     int shift = 0;
-    while (shift < 63 && ((total - 1) >> shift) >= static_cast<uint64_t>(kOrderBuckets)) shift++;
+    while (shift < 63 && ((total - 1) >> shift) >= ranges) shift++;
     uint32_t *hist_runs = reinterpret_cast<uint32_t *>(scratch);
     uint32_t *totals = reinterpret_cast<uint32_t *>(scratch + kOrderHist);
+    // per sample of a chunk: the sorted ids, the first pass's ids, the
+    // bucket byte, the high byte and the high byte in first-pass order
     uint32_t *ids = reinterpret_cast<uint32_t *>(scratch + kOrderHeader);
-    uint8_t *bkt = reinterpret_cast<uint8_t *>(scratch + kOrderHeader + chunk * sizeof(uint32_t));
+    uint32_t *ids1 = ids + chunk;
+    uint8_t *bkt = reinterpret_cast<uint8_t *>(ids1 + chunk);
+    uint8_t *high = bkt + chunk;
+    uint8_t *high1 = high + chunk;
     int per_sm = g->tune.blocks_per_sm;
     if (per_sm <= 0) {
         int occ = 0;
@@ -312,30 +285,32 @@ static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
             uint64_t blocks = (kk + BLOCK - 1) / BLOCK;
             if (blocks > full) blocks = full;
             k_order_count<SAMPLER><<<(unsigned)runs, kOrderThreads, 0, s>>>(total, kk, seed, first_id, shift, per,
-                                                                         hist_runs, bkt);
+                                                                         hist_runs, bkt, two_pass ? high : nullptr);
             PS_LAUNCH_CHECK();
             k_order_offsets<<<kOrderBuckets, kOrderBuckets, 0, s>>>(static_cast<int>(runs), hist_runs, totals);
             PS_LAUNCH_CHECK();
-            k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, bkt, ids);
-            PS_LAUNCH_CHECK();
-            if (PS_SPLIT && ADJ == kAdjHash) {
-                int4 *tup = reinterpret_cast<int4 *>(
-                    (reinterpret_cast<uintptr_t>(bkt + chunk) + 15) & ~static_cast<uintptr_t>(15));
-                int occ_a = 0, occ_b = 0;
-                PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_draw_tuples<SAMPLER, BLOCK>, BLOCK, 0));
-                PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_test_tuples<SAMPLER, BLOCK>, BLOCK, 0));
-                uint64_t ba = (kk + BLOCK - 1) / BLOCK, bb = ba;
-                if (ba > (uint64_t)g->sm_count * (occ_a > 0 ? occ_a : 1)) ba = (uint64_t)g->sm_count * (occ_a > 0 ? occ_a : 1);
-                if (bb > (uint64_t)g->sm_count * (occ_b > 0 ? occ_b : 1)) bb = (uint64_t)g->sm_count * (occ_b > 0 ? occ_b : 1);
-                k_draw_tuples<SAMPLER, BLOCK><<<(unsigned)ba, BLOCK, 0, s>>>(g->dev, kk, seed, first_id, ids, tup, hist);
-                PS_LAUNCH_CHECK();
-                k_test_tuples<SAMPLER, BLOCK><<<(unsigned)bb, BLOCK, 0, s>>>(g->dev, kk, tup, hist);
+            if (!two_pass) {
+                k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, bkt, nullptr,
+                                                                         nullptr, ids, nullptr);
                 PS_LAUNCH_CHECK();
             } else {
-                k_sample_ordered<SAMPLER, BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id,
-                                                                                        ids, hist);
+                // least significant byte first, then the high byte: every id
+                // ends in its 16-bit range of r (in range order; within a range
+                // the order of a tile's ids is free)
+                k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, bkt, nullptr,
+                                                                         high, ids1, high1);
+                PS_LAUNCH_CHECK();
+                k_order_count_bytes<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, high1, hist_runs);
+                PS_LAUNCH_CHECK();
+                k_order_offsets<<<kOrderBuckets, kOrderBuckets, 0, s>>>(static_cast<int>(runs), hist_runs, totals);
+                PS_LAUNCH_CHECK();
+                k_order_scatter<<<(unsigned)runs, kOrderThreads, 0, s>>>(kk, per, hist_runs, totals, high1, ids1,
+                                                                         nullptr, ids, nullptr);
                 PS_LAUNCH_CHECK();
             }
+            k_sample_ordered<SAMPLER, BLOCK, ADJ><<<(unsigned)blocks, BLOCK, 0, s>>>(g->dev, kk, seed, first_id, ids,
+                                                                                    hist);
+            PS_LAUNCH_CHECK();
         }
         k -= kk;
         first_id += kk;
@@ -365,20 +340,19 @@ static int ordered_s(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
     }
 }
 
-// Bytes per sample of a chunk: its sorted id and its bucket (and, for the
-// split samplers, its 16-byte tuple, 16-byte aligned).
-constexpr size_t kOrderPerSample = sizeof(uint32_t) + sizeof(uint8_t) + (PS_SPLIT ? sizeof(int4) : 0);
-constexpr size_t kOrderSlack = PS_SPLIT ? 16 : 0;
+// Bytes per sample of a chunk: its sorted id, its id after the first of two
+// passes, its bucket byte and its high byte in both orders.
+constexpr size_t kOrderPerSample = 2 * sizeof(uint32_t) + 3 * sizeof(uint8_t);
 
 size_t ordered_scratch_bytes(uint64_t k_chunk) {
     if (k_chunk == 0 || k_chunk > kOrderMaxChunk) return 0;
-    return kOrderHeader + kOrderSlack + static_cast<size_t>(k_chunk) * kOrderPerSample;
+    return kOrderHeader + static_cast<size_t>(k_chunk) * kOrderPerSample;
 }
 
 int launch_ordered(const ps_graph *g, int sampler, uint64_t k, uint64_t seed, uint64_t first_id, uint64_t *d_hist,
                    void *d_scratch, size_t scratch_bytes, cudaStream_t s) {
     if (scratch_bytes < ordered_scratch_bytes(1)) return PS_ERR_WORKSPACE;
-    uint64_t chunk = (scratch_bytes - kOrderHeader - kOrderSlack) / kOrderPerSample;
+    uint64_t chunk = (scratch_bytes - kOrderHeader) / kOrderPerSample;
     if (chunk > kOrderMaxChunk) chunk = kOrderMaxChunk;
     if (g->tune.draw_order < 0 || (g->tune.draw_order == 0 && g->m < kOrderMinEdges))
         return launch_sampler(g, sampler, k, seed, first_id, d_hist, s);

@@ -11,6 +11,10 @@
 
 namespace ps {
 
+#ifndef PS_VROW_HINT
+#define PS_VROW_HINT 0
+#endif
+
 // Alg. 1 up to the induced subgraph: the edge e drawn with probability
 // tau_e / W and the two neighbours u' (of u, not v) and v' (of v, not u).
 __device__ __forceinline__ void path3_draw(const GraphDev &g, uint64_t seed, uint64_t id, EdgeRec &e, int32_t &up,
@@ -28,7 +32,15 @@ __device__ __forceinline__ void path3_draw(const GraphDev &g, uint64_t seed, uin
     const int32_t pa = (a == static_cast<uint32_t>(e.iu)) ? e.du - 1 : static_cast<int32_t>(a);
     const int32_t pb = (b == static_cast<uint32_t>(e.jv)) ? e.dv - 1 : static_cast<int32_t>(b);
     up = ldg_i32(g.col + e.ou + pa);
+#if PS_VROW_HINT
+    // the rows of hub labels are a small, much-read part of the adjacency
+    // lists: ask L2 to keep them
+    vp = e.v >= g.hub_start ? static_cast<int32_t>(ld_hub_word(reinterpret_cast<const uint32_t *>(g.col + e.ov + pb),
+                                                                l2_keep_policy()))
+                            : ldg_i32(g.col + e.ov + pb);
+#else
     vp = ldg_i32(g.col + e.ov + pb);
+#endif
 }
 
 // Class of a 3-path u'-u-v-v' (u' != v') from its three other pairs
