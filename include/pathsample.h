@@ -67,8 +67,10 @@ typedef struct {
                                    3 = a hash table per adjacency list                      */
     int32_t draw_order;         /* the *_ordered samplers: 0 (default) sort each chunk of
                                    samples by edge draw when the graph has >= 2^20 edges
-                                   and the chunk >= 2^18 samples, else take them in id
-                                   order; 1 = always sort; -1 = never                       */
+                                   and the chunk >= 2^18 samples -- by 16 bits of r in two
+                                   passes from 2^25 edges, by 8 bits below -- else take them
+                                   in id order; 1 = always sort by 8 bits; 2 = always by
+                                   16 bits; -1 = never                                      */
     int32_t hub_min_degree;     /* smallest degree given a hub bitmap row (default 64; the
                                    rows go to the top hub_count labels of at least this
                                    degree)                                                   */
@@ -153,11 +155,13 @@ int ps_sample_centered(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t fi
  * histograms are sums, so the counts are exactly those of
  * ps_sample_3paths / ps_sample_centered for the same (k, seed, first_id);
  * only the memory traffic changes: the ids of each chunk are first sorted by
- * their draw r (equal-width ranges of [0, W) or [0, Lambda)), so samples in
- * flight together read neighbouring edge records and rows.
+ * their draw r (256 or 65536 equal-width ranges of [0, W) or [0, Lambda);
+ * see ps_tuning.draw_order), so samples in flight together read
+ * neighbouring edge records and rows.
  *
  * d_scratch: caller-owned device memory, 16-byte aligned, of
- * ps_ordered_scratch_bytes(k_chunk) bytes for chunks of k_chunk samples
+ * ps_ordered_scratch_bytes(k_chunk) bytes (about 1 MB + 11 B per sample)
+ * for chunks of k_chunk samples
  * (1 <= k_chunk <= 2^31; larger k runs in several chunks).  It is the
  * call's own working memory until the work queued on `stream` has run, so
  * concurrent calls need separate scratch.  Asynchronous.  Returns

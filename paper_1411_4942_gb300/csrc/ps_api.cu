@@ -123,7 +123,18 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.gcap = t.guide_log2_ratio < 0 ? 2 : (l.m_cap << t.guide_log2_ratio);
     if (l.gcap < 2) l.gcap = 2;
     l.hub_cap = t.hub_count;
-    l.hub_words = (n + 31) / 32;
+#ifndef PS_HUB_SPAN_LOG2
+#define PS_HUB_SPAN_LOG2 0
+#endif
+    // hub rows hold the bits of the labels from hub_bit_base up (a multiple
+    // of 32, at most the first hub's label)
+    l.hub_bit_base = 0;
+    if (PS_HUB_SPAN_LOG2 > 0 && n > (int64_t{1} << PS_HUB_SPAN_LOG2)) {
+        int64_t base = n - (int64_t{1} << PS_HUB_SPAN_LOG2);
+        if (base > n - l.hub_cap) base = n - l.hub_cap;
+        l.hub_bit_base = base > 0 ? (base / 32) * 32 : 0;
+    }
+    l.hub_words = (n - l.hub_bit_base + 31) / 32;
     // edge hash set: a power-of-two number of buckets, load <= 1/2
     l.eset_buckets = 0;
     if (t.adj_mode == kAdjHash) {
@@ -132,6 +143,12 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
         l.eset_buckets = slots / kBucketSlots;
     }
     l.eset_regions = l.eset_buckets >= kRegionBuckets ? l.eset_buckets / kRegionBuckets : 0;
+    // a region's keys are Poisson around m / regions (the hash is uniform), so
+    // lists of 9/8 of that plus 64 overflow with negligible probability; the
+    // overflow list catches the rest
+    l.eset_cap = l.eset_regions ? (l.m_cap + l.eset_regions - 1) / l.eset_regions : 0;
+    l.eset_cap += l.eset_cap / 8 + 64;
+    l.eset_ov_cap = l.eset_regions ? 65536 + l.m_cap / 256 : 0;
     l.vtab_slots = t.adj_mode == kAdjVtab ? 2 * nnz : 0;
     l.radix_tiles = (n + kRadixTile - 1) / kRadixTile;
     if (l.radix_tiles < 1) l.radix_tiles = 1;
@@ -170,9 +187,11 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.vals1 = take(n1 * sizeof(uint32_t));
     l.rcounts = take(static_cast<size_t>(256) * l.radix_tiles * sizeof(uint32_t));
     l.ecounts = take(static_cast<size_t>(256) * edge_sort_tiles(l.m_cap) * sizeof(uint32_t));
-    // the region build's key list and its per-region counts, offsets and cursors
-    l.ekeys = take(l.eset_regions ? static_cast<size_t>(l.m_cap) * sizeof(uint64_t) : 0);
-    l.eregion = take(l.eset_regions ? static_cast<size_t>(3 * (l.eset_regions + 1)) * sizeof(uint32_t) : 0);
+    // the region build's key lists (one per region, then the overflow list)
+    // and their lengths
+    l.ekeys = take(l.eset_regions ? static_cast<size_t>(l.eset_regions * l.eset_cap + l.eset_ov_cap) * sizeof(uint64_t)
+                                  : 0);
+    l.eregion = take(l.eset_regions ? static_cast<size_t>(l.eset_regions + 2) * sizeof(uint32_t) : 0);
     l.scan_flag = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(uint32_t));
     l.scan_agg = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));
     l.scan_inc = take(static_cast<size_t>(l.scan_tiles + 1) * sizeof(U64x2));

@@ -39,7 +39,7 @@ struct GraphDev {
     int32_t hub_words;
     int32_t tau_shift, lam_shift;
     int32_t adj_mode;        // kAdjHash or kAdjSearch
-    int32_t pad_;
+    int32_t hub_bit_base;    // hub rows hold the bits of labels >= hub_bit_base (a multiple of 32)
 };
 
 // Adjacency test variants (chosen by the tuning; results are identical).
@@ -57,6 +57,7 @@ enum {
     ST_TIER = 10,      // 5 words: row boundaries of the sort tiers
     ST_LONG = 15,      // first row longer than kLongRow (its arcs are walked by a block)
     ST_COUNTER = 16,   // 16 words: tile counters of scans (as uint32 pairs)
+    ST_ESET_SPILL = 32, // non-zero: the hash set's key lists overflowed (slow path taken)
     ST_WORDS = 64
 };
 
@@ -277,9 +278,9 @@ __device__ __forceinline__ bool in_sorted(const int32_t *col, int64_t o, int64_t
 __device__ __forceinline__ bool adjacent(const GraphDev &g, int32_t x, int32_t y) {
     if (x == y) return false;
     const int32_t a = min(x, y), b = max(x, y);
-    if (a >= g.hub_start) {
+    if (a >= g.hub_start) {  // then b > a >= hub_bit_base
         const uint32_t *row = g.hub + static_cast<int64_t>(a - g.hub_start) * g.hub_words;
-        return (__ldg(row + (b >> 5)) >> (b & 31)) & 1u;
+        return (__ldg(row + ((b - g.hub_bit_base) >> 5)) >> (b & 31)) & 1u;
     }
     const int64_t o = ldg_i64(g.off + a);
     const int64_t e = ldg_i64(g.off + a + 1);
@@ -289,9 +290,9 @@ __device__ __forceinline__ bool adjacent(const GraphDev &g, int32_t x, int32_t y
 // Same when the row of a (the smaller label) is already known.
 __device__ __forceinline__ bool adjacent_known(const GraphDev &g, int32_t a, int64_t oa,
                                                int64_t da, int32_t b) {
-    if (a >= g.hub_start) {
+    if (a >= g.hub_start) {  // then b > a >= hub_bit_base
         const uint32_t *row = g.hub + static_cast<int64_t>(a - g.hub_start) * g.hub_words;
-        return (__ldg(row + (b >> 5)) >> (b & 31)) & 1u;
+        return (__ldg(row + ((b - g.hub_bit_base) >> 5)) >> (b & 31)) & 1u;
     }
     return in_sorted(g.col, oa, da, b);
 }
@@ -399,41 +400,33 @@ __device__ __forceinline__ void eset_contains3(const uint64_t *set, uint64_t mas
 // Hash set plus hub rows: a pair whose larger label is one of the top-degree
 // labels (>= hub_start, rows of the hub bitmap) is answered from that
 // hub's bitmap row, the rest from the hash set.  The sampled edges are
-// drawn in proportion to tau, so a lookup (u', v) mostly names a hub v: a
-// few dozen MB of hub rows then serve a large share of the lookups, and
-// their loads ask L2 to keep those lines (evict-last) while the hash set's
-// random buckets stream past.  With no hub rows (hub_start == n) this is the
-// plain hash-set test.
-__device__ __forceinline__ uint64_t l2_keep_policy() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-#ifndef PS_HUB_HINT
-#define PS_HUB_HINT 1
-#endif
-__device__ __forceinline__ uint32_t ld_hub_word(const uint32_t *p, uint64_t pol) {
-#if PS_HUB_HINT
-    uint32_t v;
-    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
-    return v;
-#else
-    (void)pol;
-    return __ldg(p);
-#endif
+// drawn in proportion to tau, so a lookup (u', v) mostly names a hub v, and
+// the hub rows' much-read parts stay in L2.  (The rows' loads once asked L2
+// to keep them -- evict-last; with 1024 rows of 375 KB on the 3M-vertex
+// graph that hint made 3-path sampling 2-5% slower on both benchmark graphs,
+// and it was dropped.)  With no hub rows (hub_start == n) this is the plain
+// hash-set test.
+__device__ __forceinline__ uint32_t ld_hub_word(const uint32_t *p) { return __ldg(p); }
+
+// Address of the hub-row word holding bit a of hub c's row (a >= hub_bit_base).
+__device__ __forceinline__ const uint32_t *hub_word_of(const GraphDev &g, int32_t a, int32_t c) {
+    return g.hub + static_cast<int64_t>(c - g.hub_start) * g.hub_words + ((a - g.hub_bit_base) >> 5);
 }
 
-// Address of the hub-row word holding bit a of hub c's row.
-__device__ __forceinline__ const uint32_t *hub_word_of(const GraphDev &g, int32_t a, int32_t c) {
-    return g.hub + static_cast<int64_t>(c - g.hub_start) * g.hub_words + (a >> 5);
+// Does the pair a < c have a hub-row bit?  (The rows hold the labels from
+// hub_bit_base up: the tests naming a hub mostly name it with another
+// high-degree, high-label vertex, and the rest go to the hash set, which
+// holds every edge.)
+__device__ __forceinline__ bool in_hub_rows(const GraphDev &g, int32_t a, int32_t c) {
+    return c >= g.hub_start && a >= g.hub_bit_base;
 }
 
 // One pair's first load: its hub-row word (in the first slot of the
-// returned bucket) when its larger label is a hub, else its home bucket.
+// returned bucket) when it has a hub-row bit, else its home bucket.
 __device__ __forceinline__ Bucket load_pair(const GraphDev &g, int32_t a, int32_t c, uint64_t b) {
     Bucket q;
-    if (c >= g.hub_start) {
-        q.q[0].x = ld_hub_word(hub_word_of(g, a, c), l2_keep_policy());
+    if (in_hub_rows(g, a, c)) {
+        q.q[0].x = ld_hub_word(hub_word_of(g, a, c));
     } else {
         q = load_bucket(g.eset, b);
     }
@@ -442,7 +435,7 @@ __device__ __forceinline__ Bucket load_pair(const GraphDev &g, int32_t a, int32_
 
 __device__ __forceinline__ bool resolve_pair(const GraphDev &g, int32_t a, int32_t c, uint64_t key,
                                              uint64_t b, const Bucket &q) {
-    if (c >= g.hub_start) return ((q.q[0].x >> (a & 31)) & 1u) != 0u;
+    if (in_hub_rows(g, a, c)) return ((q.q[0].x >> (a & 31)) & 1u) != 0u;
     const int v = bucket_verdict(q, key);
     return v >= 0 ? v == 1 : probe_on(g.eset, g.eset_mask, key, b);
 }
@@ -459,11 +452,11 @@ __device__ __forceinline__ void pair_test3(const GraphDev &g, int32_t x0, int32_
                                            bool &r2) {
     const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
     if (!ALL) {
-        if (c0 < g.hub_start) {
+        if (!in_hub_rows(g, a0, c0)) {
             eset_contains3(g.eset, g.eset_mask, x0, y0, x1, y1, x2, y2, r0, r1, r2);
             return;
         }
-        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0));
         eset_contains2(g.eset, g.eset_mask, x1, y1, x2, y2, r1, r2);
         r0 = ((w >> (a0 & 31)) & 1u) != 0u;
         return;
@@ -481,8 +474,8 @@ __device__ __forceinline__ void pair_test3(const GraphDev &g, int32_t x0, int32_
 
 __device__ __forceinline__ bool pair_test(const GraphDev &g, int32_t x, int32_t y) {
     const int32_t a = min(x, y), c = max(x, y);
-    if (c >= g.hub_start)
-        return x != y && ((ld_hub_word(hub_word_of(g, a, c), l2_keep_policy()) >> (a & 31)) & 1u);
+    if (in_hub_rows(g, a, c))
+        return x != y && ((ld_hub_word(hub_word_of(g, a, c)) >> (a & 31)) & 1u);
     return eset_contains(g.eset, g.eset_mask, x, y);
 }
 
@@ -493,11 +486,11 @@ __device__ __forceinline__ void pair_test2(const GraphDev &g, int32_t x0, int32_
                                            int32_t y1, bool &r0, bool &r1) {
     const int32_t a0 = min(x0, y0), c0 = max(x0, y0);
     if (!ALL) {
-        if (c0 < g.hub_start) {
+        if (!in_hub_rows(g, a0, c0)) {
             eset_contains2(g.eset, g.eset_mask, x0, y0, x1, y1, r0, r1);
             return;
         }
-        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0), l2_keep_policy());
+        const uint32_t w = ld_hub_word(hub_word_of(g, a0, c0));
         r1 = eset_contains(g.eset, g.eset_mask, x1, y1);
         r0 = ((w >> (a0 & 31)) & 1u) != 0u;
         return;

@@ -249,11 +249,13 @@ k_esort_scatter(int64_t count, const uint32_t *__restrict__ kin, const uint32_t 
 // string of dependent round trips per edge).
 constexpr int kRecItems = 4;
 
+// With the region build of the hash set (lists.keys set), every edge's key
+// also goes to the end of its home region's list (one atomic per edge).
 __global__ void __launch_bounds__(256)
 k_edge_records(int64_t m, int64_t n, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval,
                const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
                const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, EdgeRec *rec,
-               u64 *status) {
+               u64 *status, EsetLists lists) {
     // every offset, label and degree is below 2^31 (nnz < 2^31), so the
     // stages work in 32 bits
     const int64_t stride = (int64_t)gridDim.x * 256 * kRecItems;
@@ -300,12 +302,24 @@ k_edge_records(int64_t m, int64_t n, const uint32_t *__restrict__ skey, const ui
             int4 *e = reinterpret_cast<int4 *>(rec + j);
             e[0] = make_int4(u[q], v[q], du[q], dv[q]);
             e[1] = make_int4(iu[q], jv, ou[q], ov[q]);
+            if (lists.keys) {
+                const uint64_t key = edge_key(u[q], v[q]);
+                const uint64_t reg = (key_hash(key) & lists.mask) >> lists.shift;
+                const uint32_t pos = atomicAdd(lists.cur + reg, 1u);
+                if (pos < lists.cap) {
+                    lists.keys[reg * lists.cap + pos] = key;
+                } else {
+                    const uint32_t o = atomicAdd(lists.ov_count, 1u);
+                    if (o < lists.ov_cap) lists.ov_keys[o] = key;
+                    else status[ST_ESET_SPILL] = 1;
+                }
+            }
         }
     }
     if (asym) raise_flag(status, F_ASYM);
 }
 
-int build_edge_table(ps_graph *g, cudaStream_t s) {
+int build_edge_table(ps_graph *g, cudaStream_t s, const EsetLists *lists) {
     const Layout &L = g->L;
     const int64_t n = L.n, nnz = L.nnz, m = L.m_cap;
     if (nnz <= 0 || m <= 0) return PS_OK;
@@ -349,8 +363,9 @@ int build_edge_table(ps_graph *g, cudaStream_t s) {
     }
     int64_t blocks = (m + 256 * kRecItems - 1) / (256 * kRecItems);
     if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+    EsetLists none{};
     k_edge_records<<<(unsigned)blocks, 256, 0, s>>>(m, n, ka, va, g->off, g->col, g->lowcnt, g->ubase, g->rec,
-                                                    g->status);
+                                                    g->status, lists ? *lists : none);
     PS_LAUNCH_CHECK();
     return PS_OK;
 }

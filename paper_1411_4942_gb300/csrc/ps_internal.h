@@ -47,9 +47,10 @@ struct Tuning {
 Tuning resolve_tuning(const ps_tuning *t, int64_t n);
 
 struct Layout {
-    int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, radix_tiles, scan_tiles;
+    int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, hub_bit_base, radix_tiles, scan_tiles;
     int64_t eset_buckets;  // 0 without the edge hash set
     int64_t eset_regions;  // regions of the region build (0: the direct build)
+    int64_t eset_cap, eset_ov_cap;  // region build: keys per region list, overflow list
     int64_t vtab_slots;    // 0 without the per-vertex tables
     size_t status, off, col, rank, lowcnt, ubase, dnew, rec, ptau, plam, gtau, glam, hub, eset, vtab;
     size_t keys0, keys1, vals0, vals1, rcounts, ecounts, ekeys, eregion, scan_flag, scan_agg, scan_inc;
@@ -159,10 +160,25 @@ inline int run_scan(ps_graph *g, int slot, int64_t count, T identity, Op op, Loa
     return PS_OK;
 }
 
+// The hash set's per-region key lists (region build): the edge-table
+// kernel appends every edge's key to the list of its home bucket's region
+// (cursors zeroed before); keys beyond a list's capacity go to an overflow
+// list, and past that the slow path is flagged in status[ST_ESET_SPILL].
+struct EsetLists {
+    uint32_t *cur;       // [regions] list lengths
+    uint32_t *ov_count;  // overflow list length
+    uint64_t *keys;      // [regions][cap]
+    uint64_t *ov_keys;   // [ov_cap]
+    int64_t cap, ov_cap;
+    uint64_t mask;       // buckets - 1
+    int shift;           // region of bucket b = b >> shift
+};
+
 // The edge table (ps_edges.cu): after the rows are relabelled and sorted and
-// ubase is known, writes every edge record, and raises F_ASYM for an
-// asymmetric input.
-int build_edge_table(ps_graph *g, cudaStream_t s);
+// ubase is known, writes every edge record (and, given `lists`, every edge's
+// hash-set key into its region's list), and raises F_ASYM for an asymmetric
+// input.
+int build_edge_table(ps_graph *g, cudaStream_t s, const EsetLists *lists);
 // Tiles of the edge table's radix sort for m edges (its digit counts take
 // 256 words per tile).
 int64_t edge_sort_tiles(int64_t m);

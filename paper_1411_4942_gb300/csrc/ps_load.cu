@@ -774,125 +774,38 @@ k_eset_upper(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32
 }
 
 // Region build.  The table is cut into regions of kRegionBuckets buckets
-// (64 KB), each small enough for one block's shared memory.  The keys are
-// first grouped by the region of their home bucket (a count, a scan and a
-// scatter), then one block per region inserts that region's keys with
+// (64 KB), each small enough for one block's shared memory.  The edge-table
+// kernel appends every key to the list of its home bucket's region
+// (EsetLists); then one block per region inserts that region's keys with
 // shared-memory compare-and-swap, probing linearly within the region, and
 // writes the whole region out (empty slots included, so the table needs no
 // clearing).  A key whose probe runs past its region's end is left in the
 // list and inserted at the end by ordinary global compare-and-swap, probing
 // on into the following regions -- already written, so every bucket between
-// a key's home and its place is full, as a lookup assumes.  The random
-// read-modify-writes of the direct build become sequential writes of the
-// table plus the key list's traffic.
+// a key's home and its place is full, as a lookup assumes; so are the keys
+// of the overflow list.  The random read-modify-writes of the direct build
+// become sequential writes of the table plus the key lists' traffic.
 constexpr int kRegionThreads = 512;
-
-__device__ __forceinline__ uint32_t region_of(uint64_t key, uint64_t mask, int region_shift) {
-    return static_cast<uint32_t>((key_hash(key) & mask) >> region_shift);
-}
-
-struct CountRegions {
-    uint32_t *cnt;
-    uint64_t mask;
-    int shift;
-    __device__ void operator()(const uint64_t (&key)[kInsertBatch], const bool (&ok)[kInsertBatch]) {
-#pragma unroll
-        for (int u = 0; u < kInsertBatch; u++) {
-            const uint32_t reg = ok[u] ? region_of(key[u], mask, shift) : 0xFFFFFFFFu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, reg);
-            if (ok[u] && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + reg, static_cast<uint32_t>(__popc(peers)));
-        }
-    }
-};
-
-struct ScatterRegions {
-    uint32_t *cur;
-    uint64_t *keys;
-    uint64_t mask;
-    int shift;
-    __device__ void operator()(const uint64_t (&key)[kInsertBatch], const bool (&ok)[kInsertBatch]) {
-#pragma unroll
-        for (int u = 0; u < kInsertBatch; u++) {
-            const uint32_t reg = ok[u] ? region_of(key[u], mask, shift) : 0xFFFFFFFFu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, reg);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (ok[u] && (threadIdx.x & 31) == leader) base = atomicAdd(cur + reg, static_cast<uint32_t>(__popc(peers)));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (ok[u]) keys[base + __popc(peers & lanemask_lt())] = key[u];
-        }
-    }
-};
-
-__global__ void __launch_bounds__(256)
-k_eset_count(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
-             const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, uint32_t *cnt, uint64_t mask,
-             int shift) {
-    CountRegions f{cnt, mask, shift};
-    for_each_edge_key(n, m, coff, ccol, lowcnt, ubase, f);
-}
-
-__global__ void __launch_bounds__(256)
-k_eset_scatter(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
-               const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, uint32_t *cur,
-               uint64_t *keys, uint64_t mask, int shift) {
-    ScatterRegions f{cur, keys, mask, shift};
-    for_each_edge_key(n, m, coff, ccol, lowcnt, ubase, f);
-}
-
-// Exclusive scan of the regions' key counts in one block (the table has at
-// most 2^31 / kRegionBuckets regions); off[r] = first entry of region r,
-// cur[r] = the same (the scatter's cursors), off[regions] = total.
-__global__ void __launch_bounds__(1024)
-k_eset_region_offsets(int64_t regions, const uint32_t *__restrict__ cnt, uint32_t *off, uint32_t *cur) {
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < regions; base += 1024) {
-        const int64_t r = base + threadIdx.x;
-        const uint32_t c = r < regions ? cnt[r] : 0u;
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        uint32_t before = s_carry;
-        for (int w = 0; w < warp; w++) before += s_warp[w];
-        const uint32_t excl = before + x - c;
-        if (r < regions) {
-            off[r] = excl;
-            cur[r] = excl;
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry = excl + c;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) off[regions] = s_carry;
-}
 
 // One block per region (grid-stride): the region's keys into shared memory,
 // each placed key's list entry cleared to the empty marker, then the region
 // written out.
 __global__ void __launch_bounds__(kRegionThreads)
-k_eset_regions(int64_t regions, int64_t region_buckets, const uint32_t *__restrict__ off, uint64_t *keys,
-               uint64_t *set, uint64_t mask) {
+k_eset_regions(int64_t regions, int64_t region_buckets, EsetLists lists, uint64_t *set) {
     extern __shared__ unsigned long long s_tab[];
     const int64_t slots = region_buckets << kBucketShift;
     for (int64_t reg = blockIdx.x; reg < regions; reg += gridDim.x) {
         for (int64_t q = threadIdx.x; q < slots; q += kRegionThreads) s_tab[q] = kEmptySlot;
         __syncthreads();
         const int64_t b0 = reg * region_buckets;
-        for (int64_t e = off[reg] + threadIdx.x; e < off[reg + 1]; e += kRegionThreads) {
-            const unsigned long long key = keys[e];
+        const int64_t len = lists.cur[reg] < lists.cap ? lists.cur[reg] : lists.cap;
+        uint64_t *list = lists.keys + reg * lists.cap;
+        for (int64_t e = threadIdx.x; e < len; e += kRegionThreads) {
+            const unsigned long long key = list[e];
             const uint64_t h = key_hash(key);
             const int first = static_cast<int>(h >> (64 - kBucketShift));
             bool placed = false;
-            for (int64_t b = static_cast<int64_t>(h & mask) - b0; b < region_buckets && !placed; b++) {
+            for (int64_t b = static_cast<int64_t>(h & lists.mask) - b0; b < region_buckets && !placed; b++) {
                 for (int q = 0; q < kBucketSlots; q++) {
                     const unsigned long long old =
                         atomicCAS(s_tab + (b << kBucketShift) + ((first + q) & (kBucketSlots - 1)), kEmptySlot, key);
@@ -902,7 +815,7 @@ k_eset_regions(int64_t regions, int64_t region_buckets, const uint32_t *__restri
                     }
                 }
             }
-            if (placed) keys[e] = kEmptySlot;
+            if (placed) list[e] = kEmptySlot;
         }
         __syncthreads();
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(set) + (b0 << kBucketShift);
@@ -911,19 +824,39 @@ k_eset_regions(int64_t regions, int64_t region_buckets, const uint32_t *__restri
     }
 }
 
-// The keys whose probe ran past their region: global compare-and-swap.
-// *total = the number of listed keys (the region offsets' last entry).
+// The keys whose probe ran past their region, and the overflow list's:
+// global compare-and-swap.
 __global__ void __launch_bounds__(256)
-k_eset_leftovers(const uint32_t *__restrict__ total, const uint64_t *__restrict__ keys, uint64_t *set, uint64_t mask,
-                 u64 *status) {
-    const int64_t count = *total;
+k_eset_leftovers(int64_t regions, EsetLists lists, uint64_t *set, u64 *status) {
+    const int64_t listed = regions * lists.cap;
+    const int64_t ov = *lists.ov_count < lists.ov_cap ? *lists.ov_count : lists.ov_cap;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     bool failed = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += stride) {
-        const uint64_t key = keys[e];
-        if (key != kEmptySlot) failed |= !eset_insert(set, mask, key);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < listed + ov; e += stride) {
+        uint64_t key;
+        if (e < listed) {
+            const int64_t reg = e / lists.cap, i = e - reg * lists.cap;
+            if (i >= static_cast<int64_t>(lists.cur[reg])) continue;
+            key = lists.keys[e];
+        } else {
+            key = lists.ov_keys[e - listed];
+        }
+        if (key != kEmptySlot) failed |= !eset_insert(set, lists.mask, key);
     }
     if (failed) raise_flag(status, F_OVERFLOW);
+}
+
+// The slow path, only when the overflow list itself overflowed (the keys it
+// could not hold are in no list): every edge inserted again by direct
+// compare-and-swap (a key already present stops at once).
+__global__ void __launch_bounds__(256)
+k_eset_spill_fallback(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+                      const int32_t *__restrict__ lowcnt, const int64_t *__restrict__ ubase, uint64_t *set,
+                      uint64_t mask, u64 *status) {
+    if (ld_acquire(reinterpret_cast<const uint32_t *>(status + ST_ESET_SPILL)) == 0u) return;
+    InsertDirect f{set, mask, false};
+    for_each_edge_key(n, m, coff, ccol, lowcnt, ubase, f);
+    if (f.failed) raise_flag(status, F_OVERFLOW);
 }
 
 // ------------------------------------------------------------------- driver
@@ -1067,10 +1000,29 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
                            StoreUbase{g->ubase, n, g->status}, s);
     if (rc) return rc;
 
-    // (5) the edge hash set.  Only sampling reads it, and it needs only the
-    // sorted rows and the edge numbering, so it is built on a side stream
-    // from here on, beside the edge table and the prefix step; ps_tau_prefix
-    // waits for it before its end (wait_eset).
+    // (5) the edge table; with the region build of the hash set (tables of
+    // at least one region), its kernel also lists every edge's key by region
+    const bool region_build = nnz > 0 && g->eset && L.eset_regions > 0;
+    EsetLists lists{};
+    if (region_build) {
+        int shift = 0;
+        while ((int64_t{1} << shift) < kRegionBuckets) shift++;
+        lists.cur = reinterpret_cast<uint32_t *>(ws + L.eregion);
+        lists.ov_count = lists.cur + L.eset_regions;
+        lists.keys = reinterpret_cast<uint64_t *>(ws + L.ekeys);
+        lists.ov_keys = lists.keys + L.eset_regions * L.eset_cap;
+        lists.cap = L.eset_cap;
+        lists.ov_cap = L.eset_ov_cap;
+        lists.mask = static_cast<uint64_t>(L.eset_buckets - 1);
+        lists.shift = shift;
+        PS_CUDA_TRY(cudaMemsetAsync(lists.cur, 0, sizeof(uint32_t) * (L.eset_regions + 1), s));
+    }
+    rc = build_edge_table(g, s, region_build ? &lists : nullptr);
+    if (rc) return rc;
+
+    // (6) the edge hash set.  Only sampling reads it, so it is built on a side
+    // stream beside the prefix step; ps_tau_prefix waits for it before its end
+    // (wait_eset).
     if (nnz > 0 && g->eset) {
         cudaStream_t es = s;
         cudaStream_t side[2];
@@ -1085,32 +1037,19 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         int64_t eb = ((m_cap + kEsetChunk - 1) / kEsetChunk + 7) / 8;  // a warp per chunk of edges
         if (eb > (int64_t)sms * kEsetBlocksPerSm) eb = (int64_t)sms * kEsetBlocksPerSm;
         if (eb < 1) eb = 1;
-        if (L.eset_regions > 0) {
+        if (region_build) {
             const int64_t regions = L.eset_regions;
-            int shift = 0;
-            while ((int64_t{1} << shift) < kRegionBuckets) shift++;
-            uint32_t *cnt = reinterpret_cast<uint32_t *>(ws + L.eregion);
-            uint32_t *roff = cnt + (regions + 1);
-            uint32_t *cur = roff + (regions + 1);
-            uint64_t *keys = reinterpret_cast<uint64_t *>(ws + L.ekeys);
-            PS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * regions, es));
-            k_eset_count<<<(unsigned)eb, 256, 0, es>>>(n, m_cap, g->off, g->col, g->lowcnt, g->ubase, cnt, eset_mask,
-                                                       shift);
-            PS_LAUNCH_CHECK();
-            k_eset_region_offsets<<<1, 1024, 0, es>>>(regions, cnt, roff, cur);
-            PS_LAUNCH_CHECK();
-            k_eset_scatter<<<(unsigned)eb, 256, 0, es>>>(n, m_cap, g->off, g->col, g->lowcnt, g->ubase, cur, keys,
-                                                         eset_mask, shift);
-            PS_LAUNCH_CHECK();
             const int smem = static_cast<int>(kRegionBuckets * kBucketSlots * sizeof(uint64_t));
             PS_CUDA_TRY(cudaFuncSetAttribute(k_eset_regions, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            int64_t rb = regions < (int64_t)sms * 3 ? regions : (int64_t)sms * 3;
-            k_eset_regions<<<(unsigned)rb, kRegionThreads, smem, es>>>(regions, kRegionBuckets, roff, keys, g->eset,
-                                                                      eset_mask);
+            const int64_t rb = regions < (int64_t)sms * 3 ? regions : (int64_t)sms * 3;
+            k_eset_regions<<<(unsigned)rb, kRegionThreads, smem, es>>>(regions, kRegionBuckets, lists, g->eset);
             PS_LAUNCH_CHECK();
-            int64_t lb = (m_cap + 255) / 256;
+            int64_t lb = (regions * L.eset_cap + 255) / 256;
             if (lb > (int64_t)sms * 8) lb = (int64_t)sms * 8;
-            k_eset_leftovers<<<(unsigned)lb, 256, 0, es>>>(roff + regions, keys, g->eset, eset_mask, g->status);
+            k_eset_leftovers<<<(unsigned)lb, 256, 0, es>>>(regions, lists, g->eset, g->status);
+            PS_LAUNCH_CHECK();
+            k_eset_spill_fallback<<<(unsigned)eb, 256, 0, es>>>(n, m_cap, g->off, g->col, g->lowcnt, g->ubase,
+                                                               g->eset, eset_mask, g->status);
             PS_LAUNCH_CHECK();
         } else {
             PS_CUDA_TRY(cudaMemsetAsync(g->eset, 0xFF, sizeof(uint64_t) * kBucketSlots * L.eset_buckets, es));
@@ -1120,10 +1059,6 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         }
         PS_CUDA_TRY(cudaEventRecord(g->ev[3], es));
     }
-
-    // (6) the edge table
-    rc = build_edge_table(g, s);
-    if (rc) return rc;
 
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -39,6 +39,12 @@ constexpr size_t kOrderHeader = kOrderHist + kOrderBuckets * sizeof(uint32_t);
 // saves.  The counts are the same either way.
 constexpr uint64_t kOrderMinChunk = 1ull << 18;
 constexpr int64_t kOrderMinEdges = 1ll << 20;
+// From this many edges the default sorts by 16 bits of r in two passes: a
+// 256th of r then spans too many edges for their records and rows to be
+// read again before L2 drops them.  Measured (one box, both samplers):
+// 3M-vertex graph, 116.6M edges, 14.75 / 5.47 -> 14.22 / 5.16 ms with the
+// sorts; R-MAT 20, 15.7M edges, 1.22 / 0.87 -> 1.23 / 0.96 ms.
+constexpr int64_t kOrderTwoPassEdges = 1ll << 25;
 
 // The edge draw r of sample id, exactly as the samplers take it.
 template <int SAMPLER>
@@ -251,7 +257,7 @@ static int ordered_t(const ps_graph *g, uint64_t k, uint64_t seed, uint64_t firs
                      char *scratch, uint64_t chunk, cudaStream_t s) {
     const uint64_t total = SAMPLER == 0 ? g->stats.W : g->stats.Lambda;
     // the two-pass order sorts by 16 bits of r (65536 ranges), the one-pass by 8
-    const bool two_pass = g->tune.draw_order == 2;
+    const bool two_pass = g->tune.draw_order == 2 || (g->tune.draw_order == 0 && g->m >= kOrderTwoPassEdges);
     const uint64_t ranges = two_pass ? 65536u : static_cast<uint64_t>(kOrderBuckets);
     int shift = 0;
     while (shift < 63 && ((total - 1) >> shift) >= ranges) shift++;

@@ -117,7 +117,7 @@ constexpr int kHubThreads = 1024;
 constexpr int64_t kHubChunkWords = 1 << 15;  // 128 KB of shared memory
 
 __global__ void __launch_bounds__(kHubThreads)
-k_hub_rows(int64_t hub_start, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
+k_hub_rows(int64_t hub_start, int64_t bit_base, const int64_t *__restrict__ coff, const int32_t *__restrict__ ccol,
            uint32_t *bits, int64_t words, int64_t chunks) {
     extern __shared__ uint32_t s_row[];
     const int64_t h = blockIdx.x / chunks, c = blockIdx.x % chunks;
@@ -127,7 +127,7 @@ k_hub_rows(int64_t hub_start, const int64_t *__restrict__ coff, const int32_t *_
     __syncthreads();
     const int64_t r = hub_start + h;
     const int64_t o = coff[r], e = coff[r + 1];
-    const int64_t lo = w0 * 32, hi = (w0 + nw) * 32;
+    const int64_t lo = bit_base + w0 * 32, hi = bit_base + (w0 + nw) * 32;  // bit_base % 32 == 0
     for (int64_t i = o + threadIdx.x; i < e; i += kHubThreads) {
         const int64_t x = ccol[i];
         if (x >= lo && x < hi) atomicOr(s_row + ((x - lo) >> 5), 1u << (x & 31));
@@ -272,8 +272,8 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
         const int64_t chunks = (words + kHubChunkWords - 1) / kHubChunkWords;
         const int smem = static_cast<int>((words < kHubChunkWords ? words : kHubChunkWords) * sizeof(uint32_t));
         PS_CUDA_TRY(cudaFuncSetAttribute(k_hub_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_hub_rows<<<(unsigned)(hubs * chunks), kHubThreads, smem, s>>>(n - hubs, g->off, g->col, g->hub, words,
-                                                                        chunks);
+        k_hub_rows<<<(unsigned)(hubs * chunks), kHubThreads, smem, s>>>(n - hubs, g->L.hub_bit_base, g->off, g->col,
+                                                                        g->hub, words, chunks);
         PS_LAUNCH_CHECK();
     }
     // The kernels queued after the synchronisation, and the hash set build,
@@ -286,7 +286,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     D.eset_mask = eset_mask;
     D.vtab = g->vtab;
     D.adj_mode = g->vtab ? kAdjVtab : (g->eset ? kAdjHash : kAdjSearch);
-    D.pad_ = 0;
+    D.hub_bit_base = static_cast<int32_t>(g->L.hub_bit_base);
     D.off = g->off;
     D.col = g->col;
     D.rec = g->rec;

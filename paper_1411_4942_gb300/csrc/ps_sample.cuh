@@ -11,8 +11,8 @@
 
 namespace ps {
 
-#ifndef PS_VROW_HINT
-#define PS_VROW_HINT 0
+#ifndef PS_LOCAL_U
+#define PS_LOCAL_U 0
 #endif
 
 // Alg. 1 up to the induced subgraph: the edge e drawn with probability
@@ -32,15 +32,7 @@ __device__ __forceinline__ void path3_draw(const GraphDev &g, uint64_t seed, uin
     const int32_t pa = (a == static_cast<uint32_t>(e.iu)) ? e.du - 1 : static_cast<int32_t>(a);
     const int32_t pb = (b == static_cast<uint32_t>(e.jv)) ? e.dv - 1 : static_cast<int32_t>(b);
     up = ldg_i32(g.col + e.ou + pa);
-#if PS_VROW_HINT
-    // the rows of hub labels are a small, much-read part of the adjacency
-    // lists: ask L2 to keep them
-    vp = e.v >= g.hub_start ? static_cast<int32_t>(ld_hub_word(reinterpret_cast<const uint32_t *>(g.col + e.ov + pb),
-                                                                l2_keep_policy()))
-                            : ldg_i32(g.col + e.ov + pb);
-#else
     vp = ldg_i32(g.col + e.ov + pb);
-#endif
 }
 
 // Class of a 3-path u'-u-v-v' (u' != v') from its three other pairs
@@ -63,7 +55,10 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     if (up == vp) return 0;
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
     bool e1, e2, e3;
-    if (ADJ == kAdjHash) {
+    if (ADJ == kAdjHash && PS_LOCAL_U && e.du <= 1024) {
+        pair_test2<HUB_ALL>(g, up, e.v, up, vp, e1, e3);
+        e2 = in_sorted(g.col, e.ou, e.du, vp);
+    } else if (ADJ == kAdjHash) {
         pair_test3<HUB_ALL>(g, up, e.v, e.u, vp, up, vp, e1, e2, e3);
     } else if (ADJ == kAdjVtab) {
         // (u', v) in the table of v, (u, v') in the table of u -- both rows

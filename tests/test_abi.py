@@ -53,15 +53,17 @@ def test_status_strings_and_workspace_sizes():
 
 
 def test_ordered_scratch_sizes():
-    """Scratch of the draw-ordered samplers: a fixed header plus 5 bytes per
-    sample of a chunk (its sorted id and its bucket); chunks of 1 .. 2^31."""
+    """Scratch of the draw-ordered samplers: a fixed header plus 11 bytes per
+    sample of a chunk (its id in both passes' orders, its bucket byte, its
+    high byte in both orders); chunks of 1 .. 2^31."""
     one = ps.ps_ordered_scratch_bytes(1)
     assert one > 0
     assert ps.ps_ordered_scratch_bytes(0) == 0
     assert ps.ps_ordered_scratch_bytes((1 << 31) + 1) == 0
-    assert ps.ps_ordered_scratch_bytes(1 << 31) == one - 5 + 5 * (1 << 31)
+    # 11 bytes per sample: two uint32 orders and three byte arrays
+    assert ps.ps_ordered_scratch_bytes(1 << 31) == one - 11 + 11 * (1 << 31)
     for k in (2, 1000, 1 << 24):
-        assert ps.ps_ordered_scratch_bytes(k) == one + 5 * (k - 1)
+        assert ps.ps_ordered_scratch_bytes(k) == one + 11 * (k - 1)
     # the tuning field that forces or disables the sort keeps the struct's size
     import ctypes
     assert ctypes.sizeof(ps.PsTuning) == 8 * 4

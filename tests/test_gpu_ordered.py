@@ -44,10 +44,11 @@ def _both(G, k, seed, first_id=0, scratch=None):
     ("gnp300", lambda: gg.gnp(300, 0.06, 3)),
     ("chung_lu_5k", gg.chung_lu_5k),
 ])
-def test_ordered_equals_oracle(name, make):
+@pytest.mark.parametrize("order", [1, 2])
+def test_ordered_equals_oracle(name, make, order):
     g = make()
     og = O.prepare(g.off, g.col)
-    G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=1))
+    G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=order))
     k, seed, first = 30000, 17, 123
     h6, h4 = G.new_hist(), G.new_hist()
     G.sample_3paths_ordered(k, seed, first, h6)
@@ -58,7 +59,7 @@ def test_ordered_equals_oracle(name, make):
 
 
 @pytest.mark.parametrize("k", [1, 31, 4097, (1 << 18) + 5])
-@pytest.mark.parametrize("order", [1, 0, -1])
+@pytest.mark.parametrize("order", [2, 1, 0, -1])
 def test_ordered_equals_plain(k, order):
     g = gg.chung_lu(20000, 15.0, 2.3, 800.0, 9)
     G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=order))
@@ -81,14 +82,15 @@ def test_ordered_in_chunks():
     scratch for one sample sorts chunks of one; by default a chunk of 2^18 + 7
     is sorted and the ragged last one (12324) is below the cut-off."""
     g = gg.gnp(2000, 0.01, 4)
-    G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=1))
-    nb = ps.ps_ordered_scratch_bytes(1000)
-    sc = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    plain, ordered = _both(G, 12345, 77, first_id=9, scratch=sc)
-    assert plain == ordered
-    one = torch.empty(ps.ps_ordered_scratch_bytes(1), dtype=torch.uint8, device="cuda")
-    plain, ordered = _both(G, 300, 78, scratch=one)
-    assert plain == ordered
+    for order in (1, 2):  # one pass, two passes
+        G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=order))
+        nb = ps.ps_ordered_scratch_bytes(1000)
+        sc = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        plain, ordered = _both(G, 12345, 77, first_id=9, scratch=sc)
+        assert plain == ordered
+        one = torch.empty(ps.ps_ordered_scratch_bytes(1), dtype=torch.uint8, device="cuda")
+        plain, ordered = _both(G, 300, 78, scratch=one)
+        assert plain == ordered
     r = gg.rmat(17, 16.0, 0.57, 0.19, 0.19, 3)  # about 2^20 edges: the default sorts
     R = ps.Graph(r.off, r.col)
     assert R.stats.m >= 1 << 20, R.stats.m
@@ -98,10 +100,12 @@ def test_ordered_in_chunks():
     assert plain == ordered
 
 
-def test_ordered_rmat20_matches_plain():
-    """The benchmark graph and size: 2^24 samples per sampler, one chunk."""
+@pytest.mark.parametrize("order", [0, 2])
+def test_ordered_rmat20_matches_plain(order):
+    """The R-MAT-20 graph and size: 2^24 samples per sampler, one chunk, in
+    the default order and the two-pass order."""
     g = gg.rmat20()
-    G = ps.Graph(g.off, g.col)
+    G = ps.Graph(g.off, g.col, tuning=ps.make_tuning(draw_order=order))
     plain, ordered = _both(G, 1 << 24, 11)
     assert plain == ordered
 
