@@ -338,7 +338,8 @@ def _run_cuda(args, g, wl, leg):
     assert n3 == k3 and nc == kc
     ps.load_library()
     chunk = args.order_chunk or min(max(k3, kc, 1), MAX_ORDER_CHUNK)
-    tuning = ps.make_tuning(adjacency=args.adjacency, hub_count=args.hub_count, draw_order=args.draw_order)
+    tuning = ps.make_tuning(adjacency=args.adjacency, hub_count=args.hub_count, draw_order=args.draw_order,
+                            hub_span_log2=args.hub_span)
 
     stream = torch.cuda.Stream(device)
     sp = stream.cuda_stream
@@ -821,6 +822,7 @@ def main():
                     help="adjacency test: 0 default (hash set), 1 hash set, 2 search + hub rows, "
                          "3 per-vertex tables")
     ap.add_argument("--hub-count", type=int, default=0, help="hub bitmap rows (0 default, -1 none)")
+    ap.add_argument("--hub-span", type=int, default=0, help="hub rows cover the top 2^k labels (0 default, -1 all)")
     ap.add_argument("--draw-order", type=int, default=0,
                     help="draw-ordered samplers: 0 by size (default), 1 one pass (256 ranges of r), "
                          "2 two passes (65536 ranges), -1 id order")

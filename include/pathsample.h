@@ -55,10 +55,11 @@ typedef struct {
     int32_t blocks_per_sm;      /* resident sampling blocks per SM (default: occupancy)      */
     int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1); -1 = none  */
     int32_t hub_count;          /* top-degree vertices (degree >= hub_min_degree) given an
-                                   adjacency bitmap row; default: up to 1024 rows within
-                                   256 MB (adjacency 2) or 512 MB (adjacency 1, where a
-                                   lookup whose larger label is a hub reads its row);
-                                   -1 = none                                                */
+                                   adjacency bitmap row; default: up to 1024 full-width
+                                   rows within 256 MB (adjacency 2), up to 8192 rows of
+                                   the hub span within 512 MB (adjacency 1, where a lookup
+                                   whose larger label is a hub and whose smaller label is
+                                   in the span reads its row); -1 = none                    */
     int32_t samples_per_thread; /* samples each thread of the batched launch keeps in flight
                                    per step of its loop: 1 (default) or 2; the other
                                    samplers take one at a time                             */
@@ -74,6 +75,9 @@ typedef struct {
     int32_t hub_min_degree;     /* smallest degree given a hub bitmap row (default 64; the
                                    rows go to the top hub_count labels of at least this
                                    degree)                                                   */
+    int32_t hub_span_log2;      /* hub rows hold the bits of the top 2^hub_span_log2 labels
+                                   only (5..30; default 19 with adjacency 1, all labels
+                                   with adjacency 2); -1 = all labels                       */
 } ps_tuning;
 
 /* Totals of one graph, filled by ps_tau_prefix. */

@@ -87,16 +87,24 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
     r.adj_mode = kAdjHash;
     r.draw_order = 0;
     if (t && (t->adjacency == kAdjSearch || t->adjacency == kAdjVtab)) r.adj_mode = t->adjacency;
-    // hub bitmap rows: up to 1024 within 256 MB for the search variant, which
-    // needs them for every hub pair; up to 1024 within 512 MB beside the hash
-    // set, where they answer the lookups naming a hub (on R-MAT 20: samplers
-    // 1.79 / 1.51 -> 1.65 / 1.29 ms, -3.4% on the whole step with their build;
-    // on the 3M-vertex graph, whose rows are 375 KB, 3-path sampling 17.13 /
-    // 16.89 / 16.08 / 15.06 / 14.81 ms with 0 / 64 / 341 / 682 / 1024 rows)
-    const int64_t row_bytes = ((n + 31) / 32) * 4;
+    // hub rows beside the hash set cover the top 2^19 labels only: a lookup
+    // whose larger label is a hub and whose smaller is among them reads one
+    // bit, the rest probe the set.  Narrower rows let more hubs share the
+    // same bytes.  The search variant needs the rows for every hub pair and
+    // keeps them full width.
+    r.hub_span_log2 = r.adj_mode == kAdjHash ? kHubSpanLog2 : 0;
+    if (t) {
+        if (t->hub_span_log2 < 0) r.hub_span_log2 = 0;
+        else if (t->hub_span_log2 > 0) r.hub_span_log2 = t->hub_span_log2 < 5 ? 5 : (t->hub_span_log2 > 30 ? 30 : t->hub_span_log2);
+    }
+    // hub bitmap rows: up to 1024 full-width rows within 256 MB for the search
+    // variant; up to kHubRowsMax within 512 MB beside the hash set
+    const int64_t span = (r.hub_span_log2 > 0 && n > (int64_t{1} << r.hub_span_log2)) ? (int64_t{1} << r.hub_span_log2) : n;
+    const int64_t row_bytes = ((span + 31) / 32) * 4;
     const int64_t budget = (r.adj_mode == kAdjSearch ? 256ll : r.adj_mode == kAdjHash ? 512ll : 0ll) << 20;
     int64_t hubs = row_bytes > 0 ? budget / row_bytes : 0;
-    if (hubs > 1024) hubs = 1024;
+    const int64_t cap = r.adj_mode == kAdjHash ? kHubRowsMax : 1024;
+    if (hubs > cap) hubs = cap;
     r.hub_count = static_cast<int>(hubs);
     if (t) {
         if (t->block_size == 128 || t->block_size == 256 || t->block_size == 512 || t->block_size == 1024)
@@ -123,14 +131,11 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.gcap = t.guide_log2_ratio < 0 ? 2 : (l.m_cap << t.guide_log2_ratio);
     if (l.gcap < 2) l.gcap = 2;
     l.hub_cap = t.hub_count;
-#ifndef PS_HUB_SPAN_LOG2
-#define PS_HUB_SPAN_LOG2 0
-#endif
     // hub rows hold the bits of the labels from hub_bit_base up (a multiple
     // of 32, at most the first hub's label)
     l.hub_bit_base = 0;
-    if (PS_HUB_SPAN_LOG2 > 0 && n > (int64_t{1} << PS_HUB_SPAN_LOG2)) {
-        int64_t base = n - (int64_t{1} << PS_HUB_SPAN_LOG2);
+    if (t.hub_span_log2 > 0 && n > (int64_t{1} << t.hub_span_log2)) {
+        int64_t base = n - (int64_t{1} << t.hub_span_log2);
         if (base > n - l.hub_cap) base = n - l.hub_cap;
         l.hub_bit_base = base > 0 ? (base / 32) * 32 : 0;
     }

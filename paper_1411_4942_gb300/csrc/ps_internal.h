@@ -25,6 +25,8 @@ constexpr int kLongRow = 128;
 // Hub rows are only worth a bitmap above this degree (default of the tuning
 // field hub_min_degree).
 constexpr int kHubMinDegree = 64;
+constexpr int kHubSpanLog2 = 19;   // default hub-row span beside the hash set
+constexpr int kHubRowsMax = 8192;  // default hub-row cap beside the hash set
 // Items per tile of every scan.
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
@@ -41,6 +43,7 @@ struct Tuning {
     int hub_count;         // 0: none
     int samples_per_thread;  // batched launch: 1 or 2
     int hub_min_degree;
+    int hub_span_log2;     // hub rows cover the top 2^span labels; 0: all labels
     int adj_mode;          // kAdjHash or kAdjSearch
     int draw_order;        // ordered samplers: 0 by size, 1 always, -1 never
 };

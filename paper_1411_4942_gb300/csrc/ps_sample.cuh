@@ -11,10 +11,6 @@
 
 namespace ps {
 
-#ifndef PS_LOCAL_U
-#define PS_LOCAL_U 0
-#endif
-
 // Alg. 1 up to the induced subgraph: the edge e drawn with probability
 // tau_e / W and the two neighbours u' (of u, not v) and v' (of v, not u).
 __device__ __forceinline__ void path3_draw(const GraphDev &g, uint64_t seed, uint64_t id, EdgeRec &e, int32_t &up,
@@ -55,10 +51,7 @@ __device__ __forceinline__ int sample_3path(const GraphDev &g, uint64_t seed, ui
     if (up == vp) return 0;
     // the path u'-u-v-v' is present; the pairs (u',v), (u,v'), (u',v') decide
     bool e1, e2, e3;
-    if (ADJ == kAdjHash && PS_LOCAL_U && e.du <= 1024) {
-        pair_test2<HUB_ALL>(g, up, e.v, up, vp, e1, e3);
-        e2 = in_sorted(g.col, e.ou, e.du, vp);
-    } else if (ADJ == kAdjHash) {
+    if (ADJ == kAdjHash) {
         pair_test3<HUB_ALL>(g, up, e.v, e.u, vp, up, vp, e1, e2, e3);
     } else if (ADJ == kAdjVtab) {
         // (u', v) in the table of v, (u, v') in the table of u -- both rows

@@ -48,7 +48,8 @@ class PsTuning(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("guide_log2_ratio", ctypes.c_int32), ("hub_count", ctypes.c_int32),
                 ("samples_per_thread", ctypes.c_int32), ("adjacency", ctypes.c_int32),
-                ("draw_order", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32)]
+                ("draw_order", ctypes.c_int32), ("hub_min_degree", ctypes.c_int32),
+                ("hub_span_log2", ctypes.c_int32)]
 
 
 class PsStats(ctypes.Structure):
@@ -366,12 +367,14 @@ ADJ_HASH, ADJ_SEARCH, ADJ_VTAB = 1, 2, 3
 
 
 def make_tuning(block_size=0, blocks_per_sm=0, guide_log2_ratio=0, hub_count=0,
-                adjacency=0, draw_order=0, samples_per_thread=0, hub_min_degree=0) -> PsTuning:
+                adjacency=0, draw_order=0, samples_per_thread=0, hub_min_degree=0,
+                hub_span_log2=0) -> PsTuning:
     t = PsTuning()
     t.block_size, t.blocks_per_sm = block_size, blocks_per_sm
     t.guide_log2_ratio, t.hub_count = guide_log2_ratio, hub_count
     t.adjacency, t.draw_order = adjacency, draw_order
     t.samples_per_thread, t.hub_min_degree = samples_per_thread, hub_min_degree
+    t.hub_span_log2 = hub_span_log2
     return t
 
 

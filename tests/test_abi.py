@@ -50,6 +50,11 @@ def test_status_strings_and_workspace_sizes():
     t_off = ps.make_tuning(hub_count=-1, guide_log2_ratio=-1)
     assert ps.ps_graph_workspace_bytes(100000, 1000000, t_off) < ps.ps_graph_workspace_bytes(100000, 1000000)
     assert ps.ps_end_to_end_workspace_bytes(1000, 10000) > a
+    # 1024 hub rows over the top 2^20 of 2^22 labels take 128 MB, full-width rows 512 MB
+    n, nnz = 1 << 22, 1 << 24
+    narrow = ps.ps_graph_workspace_bytes(n, nnz, ps.make_tuning(hub_count=1024, hub_span_log2=20))
+    full = ps.ps_graph_workspace_bytes(n, nnz, ps.make_tuning(hub_count=1024, hub_span_log2=-1))
+    assert full - narrow == 1024 * 4 * ((n >> 5) - (1 << 15))
 
 
 def test_ordered_scratch_sizes():
@@ -64,7 +69,8 @@ def test_ordered_scratch_sizes():
     assert ps.ps_ordered_scratch_bytes(1 << 31) == one - 11 + 11 * (1 << 31)
     for k in (2, 1000, 1 << 24):
         assert ps.ps_ordered_scratch_bytes(k) == one + 11 * (k - 1)
-    # the tuning field that forces or disables the sort keeps the struct's size
+    # nine int32 tuning fields, the last one the hub-row span
     import ctypes
-    assert ctypes.sizeof(ps.PsTuning) == 8 * 4
+    assert ctypes.sizeof(ps.PsTuning) == 9 * 4
     assert ps.make_tuning(draw_order=-1).draw_order == -1
+    assert ps.make_tuning(hub_span_log2=-1).hub_span_log2 == -1

@@ -209,6 +209,12 @@ def test_tunings_do_not_change_results():
     for t in (None, ps.make_tuning(block_size=128, guide_log2_ratio=-1, hub_count=-1),
               ps.make_tuning(block_size=512, blocks_per_sm=1, guide_log2_ratio=4, hub_count=2000),
               ps.make_tuning(block_size=1024, hub_count=5),
+              # hub rows over part of the labels: rows start at the span's base,
+              # at the first hub (2000 hubs, 1024-label span), or cover 32 labels
+              ps.make_tuning(hub_count=4000, hub_span_log2=12, hub_min_degree=2),
+              ps.make_tuning(hub_count=2000, hub_span_log2=10, hub_min_degree=1),
+              ps.make_tuning(hub_count=31, hub_span_log2=5),
+              ps.make_tuning(hub_count=3000, hub_span_log2=11, adjacency=ps.ADJ_SEARCH),
               ps.make_tuning(adjacency=ps.ADJ_SEARCH),
               ps.make_tuning(block_size=128, guide_log2_ratio=1, adjacency=ps.ADJ_SEARCH,
                              hub_count=-1),
