@@ -86,6 +86,28 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+L2_RESIDENT_BYTES = 64 << 20  # a workspace this small stays in the 129 MB L2
+
+
+def measured_l2_read(device) -> float:
+    """Read bandwidth of L2 in GB/s, measured in this run: best of 20 sums of
+    a 48 MB int32 tensor that stays in L2 (a streaming read; the samplers'
+    random 32-byte reads are served at or below it)."""
+    import torch
+    x = torch.ones(12 << 20, dtype=torch.int32, device=device)
+    for _ in range(3):
+        x.sum()
+    best = float("inf")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(20):
+        e0.record()
+        x.sum()
+        e1.record()
+        torch.cuda.synchronize(device)
+        best = min(best, e0.elapsed_time(e1))
+    return x.numel() * 4 / (best / 1e3) / 1e9
+
+
 def kernel_source_tag() -> str:
     h = hashlib.sha1()
     for name in ("ps_sample.cuh", "ps_device.cuh", "ps_sample.cu", "ps_order.cu"):
@@ -426,6 +448,15 @@ def _run_cuda(args, g, wl, leg):
     load_bytes = BYTES_LOAD_PER_EDGE * st.m
     achieved_load = load_bytes / (statistics.mean(prep_ms) / 1e3) / 1e9
     traffic = ncu_traffic(args.workload)
+    # a graph whose whole workspace fits in L2: the samplers against L2 too
+    roof_l2 = None
+    if nb <= L2_RESIDENT_BYTES:
+        l2 = measured_l2_read(device)
+        roof_l2 = {"bound": "l2", "achieved": achieved, "achieved_centred": achieved_c, "peak": l2,
+                   "unit": "GB/s", "frac": achieved / l2, "frac_centred": achieved_c / l2,
+                   "workspace_bytes": nb,
+                   "peak_source": "measured in this run: best of 20 torch sums of a 48 MB int32 tensor held "
+                                  "in L2 (streaming read bandwidth)"}
 
     # end to end through the host-buffer call (inputs copied from pinned memory every step)
     e2e = None
@@ -485,6 +516,7 @@ def _run_cuda(args, g, wl, leg):
                               "unit": "GB/s", "frac": achieved_load / peak,
                               "bytes_per_edge": BYTES_LOAD_PER_EDGE,
                               "kernel": "ps_load_csr + ps_tau_prefix (all kernels, sorts included)"},
+            "roofline_l2": roof_l2,
             "order_chunk": chunk,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps, "clocks": clk,

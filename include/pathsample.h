@@ -53,13 +53,15 @@ typedef struct CUstream_st *ps_stream_t; /* same type as cudaStream_t */
 typedef struct {
     int32_t block_size;         /* sampling threads per block: 128, 256 (default), 512, 1024 */
     int32_t blocks_per_sm;      /* resident sampling blocks per SM (default: occupancy)      */
-    int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1); -1 = none  */
+    int32_t guide_log2_ratio;   /* guide buckets ~ m * 2^ratio, 1..4 (default 1, or m / 4
+                                   buckets on graphs of 2^25 edges and more); -1 = none     */
     int32_t hub_count;          /* top-degree vertices (degree >= hub_min_degree) given an
                                    adjacency bitmap row; default: up to 1024 full-width
                                    rows within 256 MB (adjacency 2), up to 8192 rows of
-                                   the hub span within 512 MB (adjacency 1, where a lookup
-                                   whose larger label is a hub and whose smaller label is
-                                   in the span reads its row); -1 = none                    */
+                                   the hub span within 512 MB and 48 bytes per edge
+                                   (adjacency 1, where a lookup whose larger label is a hub
+                                   and whose smaller label is in the span reads its row);
+                                   -1 = none                                                */
     int32_t samples_per_thread; /* samples each thread of the batched launch keeps in flight
                                    per step of its loop: 1 (default) or 2; the other
                                    samplers take one at a time                             */
@@ -107,8 +109,9 @@ size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
  * vertex by its rank in the order "d_u < d_v, ties by smaller id" (so the
  * order becomes integer order), rebuilds the adjacency lists sorted
  * ascending, and builds the edge table (u < v, u ascending then v ascending)
- * with the positions of each edge in both endpoint lists, the raw weights
- * tau_e and lambda_e, and (default adjacency) the hash set of the edges.
+ * with the positions of each edge in both endpoint lists, the inclusive
+ * uint64 prefix sums of the weights tau_e and lambda_e (in the same pass as
+ * the table), and (default adjacency) the hash set of the edges.
  *
  * d_off / d_col belong to the caller and are only read during the call.
  * d_workspace (ws_bytes >= ps_graph_workspace_bytes(n, nnz, t), 256-byte
@@ -127,16 +130,17 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
                 ps_graph **out);
 
 /* Section 3 (tau_e, W) and Section 4 (lambda_e, Lambda), the edge
- * distributions of Alg. 1 and Alg. 3: turns both weights of every edge into
- * their inclusive uint64 prefix sums (exact, so the edge draw is exact),
- * computes N_1 of Alg. 2, the guide tables of the inverse-CDF search and the
- * structures of the chosen adjacency variant.  Synchronises `stream` once to
+ * distributions of Alg. 1 and Alg. 3: publishes the totals W and Lambda of
+ * the inclusive uint64 prefix sums that ps_load_csr wrote (exact, so the edge
+ * draw is exact), computes N_1 of Alg. 2, the guide tables of the
+ * inverse-CDF search and the structures of the chosen adjacency variant; no
+ * sampler may run before it.  Synchronises `stream` once to
  * read the totals and fills *out; the guide tables and adjacency structures
  * are then finished in `stream` order, so sampling on another stream must
  * first wait for `stream`.  A second call returns the same totals without
  * recomputing.  Returns PS_NO_PATHS when W == 0 or Lambda == 0
  * (sampling then leaves histograms untouched), PS_ERR_OVERFLOW when a sum
- * does not fit in 64 bits, PS_ERR_TIMEOUT when the scan's bounded wait
+ * does not fit in 64 bits, PS_ERR_TIMEOUT when a scan's bounded wait
  * expired. */
 int ps_tau_prefix(ps_graph *g, ps_stream_t stream, ps_stats *out);
 

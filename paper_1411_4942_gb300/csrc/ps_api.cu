@@ -77,11 +77,15 @@ int flags_to_status(uint64_t f) {
     return PS_OK;
 }
 
-Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
+Tuning resolve_tuning(const ps_tuning *t, int64_t n, int64_t nnz) {
     Tuning r;
     r.block_size = 256;
     r.blocks_per_sm = 0;
-    r.guide_log2_ratio = 1;
+    // guide tables: 2m buckets; m/4 from kCoarseGuideEdges edges, where the
+    // samplers take their draws in order (whole step on the 3M-vertex graph
+    // 30.91 -> 29.76 ms with m/4, 30.38 with m, 30.01 with m/16 buckets;
+    // R-MAT-20 4.32 ms either way)
+    r.guide_log2_ratio = nnz / 2 >= kCoarseGuideEdges ? -2 : 1;
     r.samples_per_thread = 1;
     r.hub_min_degree = kHubMinDegree;
     r.adj_mode = kAdjHash;
@@ -98,10 +102,12 @@ Tuning resolve_tuning(const ps_tuning *t, int64_t n) {
         else if (t->hub_span_log2 > 0) r.hub_span_log2 = t->hub_span_log2 < 5 ? 5 : (t->hub_span_log2 > 30 ? 30 : t->hub_span_log2);
     }
     // hub bitmap rows: up to 1024 full-width rows within 256 MB for the search
-    // variant; up to kHubRowsMax within 512 MB beside the hash set
+    // variant; up to kHubRowsMax within 512 MB beside the hash set, and within
+    // 48 bytes per edge there (under a third of the graph's workspace)
     const int64_t span = (r.hub_span_log2 > 0 && n > (int64_t{1} << r.hub_span_log2)) ? (int64_t{1} << r.hub_span_log2) : n;
     const int64_t row_bytes = ((span + 31) / 32) * 4;
-    const int64_t budget = (r.adj_mode == kAdjSearch ? 256ll : r.adj_mode == kAdjHash ? 512ll : 0ll) << 20;
+    int64_t budget = (r.adj_mode == kAdjSearch ? 256ll : r.adj_mode == kAdjHash ? 512ll : 0ll) << 20;
+    if (r.adj_mode == kAdjHash && budget > 24 * nnz) budget = 24 * nnz;
     int64_t hubs = row_bytes > 0 ? budget / row_bytes : 0;
     const int64_t cap = r.adj_mode == kAdjHash ? kHubRowsMax : 1024;
     if (hubs > cap) hubs = cap;
@@ -128,8 +134,12 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.n = n;
     l.nnz = nnz;
     l.m_cap = nnz / 2;
-    l.gcap = t.guide_log2_ratio < 0 ? 2 : (l.m_cap << t.guide_log2_ratio);
+    // ratio r >= 1: m << r buckets; -1: none (at most 2 buckets); r <= -2
+    // (the default on large graphs): m >> -r
+    l.gcap = t.guide_log2_ratio == -1 ? 2
+             : (t.guide_log2_ratio < 0 ? (l.m_cap >> -t.guide_log2_ratio) : (l.m_cap << t.guide_log2_ratio));
     if (l.gcap < 2) l.gcap = 2;
+    if (l.gcap > INT32_MAX - 2) l.gcap = INT32_MAX - 2;  // bucket numbers stay in 31 bits
     l.hub_cap = t.hub_count;
     // hub rows hold the bits of the labels from hub_bit_base up (a multiple
     // of 32, at most the first hub's label)
@@ -181,7 +191,9 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.rec = take(static_cast<size_t>(l.m_cap) * sizeof(EdgeRec));
     l.ptau = take(static_cast<size_t>(l.m_cap) * sizeof(uint64_t));
     l.plam = take(static_cast<size_t>(l.m_cap) * sizeof(uint64_t));
-    l.gtau = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
+    // G_tau also holds the edge sort's sorted (key, value) list during the load
+    const int64_t gtau_words = l.gcap + 2 > 2 * l.m_cap ? l.gcap + 2 : 2 * l.m_cap;
+    l.gtau = take(static_cast<size_t>(gtau_words) * sizeof(int32_t));
     l.glam = take(static_cast<size_t>(l.gcap + 2) * sizeof(int32_t));
     l.hub = take(static_cast<size_t>(l.hub_cap) * l.hub_words * sizeof(uint32_t));
     l.eset = take(static_cast<size_t>(l.eset_buckets) * kBucketSlots * sizeof(uint64_t));
@@ -276,7 +288,7 @@ int ps_selftest_bounded_wait(void *d_scratch, uint32_t spin_limit, ps_stream_t s
 
 size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t) {
     Layout L;
-    if (!make_layout(n, nnz, resolve_tuning(t, n), &L)) return 0;
+    if (!make_layout(n, nnz, resolve_tuning(t, n, nnz), &L)) return 0;
     return L.total;
 }
 
@@ -285,7 +297,7 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
     if (!out) return PS_ERR_ARG;
     *out = nullptr;
     if (n < 0 || nnz < 0 || !d_off || (nnz > 0 && !d_col)) return PS_ERR_ARG;
-    const Tuning tu = resolve_tuning(t, n);
+    const Tuning tu = resolve_tuning(t, n, nnz);
     Layout L;
     if (!make_layout(n, nnz, tu, &L)) return PS_ERR_ARG;
     if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u) != 0 || ws_bytes < L.total)
@@ -654,7 +666,7 @@ int ps_batch_sample_prepared(const void *d_table, int32_t n_graphs, const ps_wor
     if (!d_table || n_graphs <= 0 || n_items < 0 || (n_items > 0 && (!d_items || !d_hist)) || !d_counter)
         return PS_ERR_ARG;
     if (n_items > static_cast<int64_t>(UINT32_MAX) - (1 << 20)) return PS_ERR_ARG;
-    const Tuning tu = resolve_tuning(t, 0);
+    const Tuning tu = resolve_tuning(t, 0, 0);
     return launch_batch(d_table, n_graphs, d_items, n_items, d_hist, d_counter, tu,
                         reinterpret_cast<cudaStream_t>(stream));
 }

@@ -27,6 +27,7 @@ constexpr int kLongRow = 128;
 constexpr int kHubMinDegree = 64;
 constexpr int kHubSpanLog2 = 19;   // default hub-row span beside the hash set
 constexpr int kHubRowsMax = 8192;  // default hub-row cap beside the hash set
+constexpr int64_t kCoarseGuideEdges = int64_t{1} << 25;  // default guide of m/4 buckets from here
 // Items per tile of every scan.
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = 8;
@@ -39,7 +40,7 @@ constexpr int64_t kRadixTile = kRadixBlock * kRadixItems;
 struct Tuning {
     int block_size;
     int blocks_per_sm;
-    int guide_log2_ratio;  // -1: no guide
+    int guide_log2_ratio;  // >= 1: m << r buckets; -1: no guide; <= -2: m >> -r buckets
     int hub_count;         // 0: none
     int samples_per_thread;  // batched launch: 1 or 2
     int hub_min_degree;
@@ -47,7 +48,7 @@ struct Tuning {
     int adj_mode;          // kAdjHash or kAdjSearch
     int draw_order;        // ordered samplers: 0 by size, 1 always, -1 never
 };
-Tuning resolve_tuning(const ps_tuning *t, int64_t n);
+Tuning resolve_tuning(const ps_tuning *t, int64_t n, int64_t nnz);
 
 struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, hub_bit_base, radix_tiles, scan_tiles;

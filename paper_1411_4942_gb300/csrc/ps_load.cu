@@ -321,12 +321,14 @@ __device__ __forceinline__ void sort_row_warp(const RowIn &R, int64_t r, uint32_
     if (lane == 0) R.lowcnt[r] = low;
 }
 
-// Tier B: rows of 33..1024 entries, one warp, bitonic network in registers.
-// (Capped at 64 registers: four blocks per SM beat the spill-free 105-register
-// build; the same holds for tier C at three blocks.)
-__global__ void __launch_bounds__(256, 4) k_sort_tier_b(RowIn R) {
+// Tier B: rows of 33..1024 entries, one warp, bitonic network in registers,
+// in two kernels: rows up to kLongRow entries (two or four keys per lane)
+// at 32 registers and full occupancy, the longer ones capped at 64
+// registers (four blocks per SM beat the spill-free 105-register build; the
+// same holds for tier C at three blocks).
+__global__ void __launch_bounds__(256, 8) k_sort_tier_b(RowIn R) {
     const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 1]);
-    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 2]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_LONG]);
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
     bool bad = false, nsimple = false;
     for (int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < r1; r += nw) {
@@ -334,8 +336,22 @@ __global__ void __launch_bounds__(256, 4) k_sort_tier_b(RowIn R) {
         const int64_t o = ldg_i64(R.off + v);
         const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
         if (d <= 64) sort_row_warp<2>(R, r, v, o, d, bad, nsimple);
-        else if (d <= 128) sort_row_warp<4>(R, r, v, o, d, bad, nsimple);
-        else if (d <= 256) sort_row_warp<8>(R, r, v, o, d, bad, nsimple);
+        else sort_row_warp<4>(R, r, v, o, d, bad, nsimple);
+    }
+    report(R, bad, nsimple);
+}
+static_assert(kLongRow == 128 && kLongRow < kTierB, "tier B's first kernel sorts rows of at most 4 keys per lane");
+
+__global__ void __launch_bounds__(256, 4) k_sort_tier_b2(RowIn R) {
+    const int64_t r0 = static_cast<int64_t>(R.status[ST_LONG]);
+    const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 2]);
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    bool bad = false, nsimple = false;
+    for (int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; r < r1; r += nw) {
+        const uint32_t v = R.inv[r];
+        const int64_t o = ldg_i64(R.off + v);
+        const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
+        if (d <= 256) sort_row_warp<8>(R, r, v, o, d, bad, nsimple);
         else if (d <= 512) sort_row_warp<16>(R, r, v, o, d, bad, nsimple);
         else sort_row_warp<32>(R, r, v, o, d, bad, nsimple);
     }
@@ -986,8 +1002,12 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
             k_sort_tier_c<<<sms * 4, 512, smem, fork.side(0)>>>(R);
             PS_LAUNCH_CHECK();
         }
-        k_sort_tier_b<<<sms * 4, 256, 0, s>>>(R);
+        k_sort_tier_b<<<sms * 8, 256, 0, s>>>(R);
         PS_LAUNCH_CHECK();
+        if (g->d_max > kLongRow) {
+            k_sort_tier_b2<<<sms * 4, 256, 0, s>>>(R);
+            PS_LAUNCH_CHECK();
+        }
         k_sort_tier_a<<<sms * 16, 256, 0, s>>>(R);
         PS_LAUNCH_CHECK();
         rc = fork.join();
@@ -1065,7 +1085,8 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
     const uint64_t m_upper = st[ST_M_UPPER];
     uint64_t flags = st[ST_FLAGS];
     if (2 * m_upper != static_cast<uint64_t>(nnz)) flags |= F_ASYM;
-    const int status = flags_to_status(flags);
+    // a prefix sum past 2^64 is reported by ps_tau_prefix, as documented
+    const int status = flags_to_status(flags & ~static_cast<uint64_t>(F_OVERFLOW));
     if (status != PS_OK) return status;
     g->m = static_cast<int64_t>(m_upper);
     return PS_OK;

@@ -7,38 +7,6 @@
 
 namespace ps {
 
-// tau_j = (d_u - 1)(d_v - 1); lambda_j = L_{u,v} L_{v,u} with
-// L_{u,v} = d_u - 1 - iu (the neighbours of u after v in the order).
-__device__ __forceinline__ U64x2 weights(const EdgeRec &e) {
-    const uint64_t t = static_cast<uint64_t>(e.du - 1) * static_cast<uint64_t>(e.dv - 1);
-    const uint64_t l = static_cast<uint64_t>(e.du - 1 - e.iu) * static_cast<uint64_t>(e.dv - 1 - e.jv);
-    return U64x2{t, l};
-}
-
-// The scan reads the edge records in order (the edge-table kernel writes them
-// scattered, where the 8-byte weights would be partial-sector writes).
-struct LoadWeights {
-    const EdgeRec *rec;
-    __device__ U64x2 operator()(int64_t j) const { return weights(ldg_rec(rec + j)); }
-};
-// The weights are non-negative, so a running sum that passes 2^64 shows up at
-// the first item whose inclusive prefix is below its exclusive one; the last
-// item's prefixes are W and Lambda.
-struct StorePrefix {
-    uint64_t *ptau, *plam;
-    u64 *status;
-    int64_t m;
-    __device__ void operator()(int64_t j, U64x2 exc, U64x2 inc) const {
-        ptau[j] = inc.a;
-        plam[j] = inc.b;
-        if (inc.a < exc.a || inc.b < exc.b) raise_flag(status, F_OVERFLOW);
-        if (j == m - 1) {
-            status[ST_W_LO] = inc.a;
-            status[ST_L_LO] = inc.b;
-        }
-    }
-};
-
 // N_1 = sum_v C(d_v, 3) (128-bit) and the number of hub rows: the top
 // `hub_cap` labels whose degree is at least `hub_min` (labels are in degree
 // order, so these are the last rows).
@@ -77,35 +45,48 @@ k_vertex_totals(int64_t n, const int32_t *__restrict__ dnew, int64_t hub_cap, in
 // is the edge that the first r of bucket b selects.  Edge j covers r in
 // [P[j-1], P[j] - 1], so it owns the buckets whose first r falls in that
 // range -- a contiguous run, and every bucket has exactly one owner.  Each
-// lane writes its own short run; a warp writes long runs together.
+// lane writes its own short run; a warp writes long runs together.  A warp
+// takes kGuideGroups groups of 32 edges per step with all their prefix loads
+// issued first.
+constexpr int kGuideGroups = 4;
+
 __global__ void __launch_bounds__(256)
 k_guide_fill(int64_t m, const uint64_t *__restrict__ P, int shift, int32_t *G, int64_t B) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (blockIdx.x == 0 && threadIdx.x == 0) G[B] = static_cast<int32_t>(m - 1);
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w * 32 < m; w += nw) {
-        const int64_t j = w * 32 + lane;
-        uint64_t bstart = 0, len = 0;
-        if (j < m) {
-            const uint64_t prev = j ? P[j - 1] : 0ull;
-            const uint64_t cur = P[j];
-            if (cur != prev) {
-                bstart = prev ? ((prev - 1) >> shift) + 1 : 0ull;
-                const uint64_t bend = (cur - 1) >> shift;
-                len = bstart <= bend ? bend - bstart + 1 : 0;
+    for (int64_t g0 = wid * kGuideGroups; g0 * 32 < m; g0 += nw * kGuideGroups) {
+        uint64_t prev[kGuideGroups], cur[kGuideGroups];
+#pragma unroll
+        for (int u = 0; u < kGuideGroups; u++) {
+            const int64_t j = (g0 + u) * 32 + lane;
+            prev[u] = (j >= 1 && j <= m) ? __ldg(P + j - 1) : 0ull;
+            cur[u] = j < m ? __ldg(P + j) : 0ull;
+        }
+        // bucket numbers are below B + 1 <= 2^31, so after the shift the runs
+        // are handled in 32 bits
+#pragma unroll
+        for (int u = 0; u < kGuideGroups; u++) {
+            const int64_t j = (g0 + u) * 32 + lane;
+            uint32_t bstart = 0, len = 0;
+            if (j < m && cur[u] != prev[u]) {
+                bstart = prev[u] ? static_cast<uint32_t>((prev[u] - 1) >> shift) + 1u : 0u;
+                const uint32_t bend = static_cast<uint32_t>((cur[u] - 1) >> shift);
+                len = bstart <= bend ? bend - bstart + 1u : 0u;
             }
-        }
-        if (len <= 8) {
-            for (uint64_t q = 0; q < len; q++) G[bstart + q] = static_cast<int32_t>(j);
-        }
-        uint32_t longs = __ballot_sync(0xffffffffu, len > 8);
-        while (longs) {
-            const int l = __ffs(longs) - 1;
-            longs &= longs - 1;
-            const uint64_t bs = __shfl_sync(0xffffffffu, bstart, l);
-            const uint64_t ln = __shfl_sync(0xffffffffu, len, l);
-            const int32_t jj = static_cast<int32_t>(w * 32 + l);
-            for (uint64_t q = lane; q < ln; q += 32) G[bs + q] = jj;
+            if (len <= 8) {
+                for (uint32_t q = 0; q < len; q++) G[bstart + q] = static_cast<int32_t>(j);
+            }
+            uint32_t longs = __ballot_sync(0xffffffffu, len > 8);
+            while (longs) {
+                const int l = __ffs(longs) - 1;
+                longs &= longs - 1;
+                const uint32_t bs = __shfl_sync(0xffffffffu, bstart, l);
+                const uint32_t ln = __shfl_sync(0xffffffffu, len, l);
+                const int32_t jj = static_cast<int32_t>((g0 + u) * 32 + l);
+                for (uint32_t q = lane; q < ln; q += 32) G[bs + q] = jj;
+            }
         }
     }
 }
@@ -195,8 +176,11 @@ static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *
     const int64_t B = static_cast<int64_t>(((total - 1) >> shift) + 1);
     *shift_out = shift;
     (void)slot;
-    int64_t blocks = (m + 255) / 256;
-    if (blocks > (int64_t)g->sm_count * 32) blocks = (int64_t)g->sm_count * 32;
+    // one resident wave (the loop strides over the edges)
+    int occ = 0;
+    PS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_guide_fill, 256, 0));
+    int64_t blocks = (m + 256 * kGuideGroups - 1) / (256 * kGuideGroups);
+    if (blocks > (int64_t)g->sm_count * (occ > 0 ? occ : 1)) blocks = (int64_t)g->sm_count * (occ > 0 ? occ : 1);
     k_guide_fill<<<(unsigned)blocks, 256, 0, s>>>(m, P, shift, G, B);
     PS_LAUNCH_CHECK();
     return PS_OK;
@@ -205,19 +189,10 @@ static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *
 int prefix_graph(ps_graph *g, cudaStream_t s) {
     const int64_t n = g->n, m = g->m;
     const int sms = g->sm_count;
-    PS_CUDA_TRY(cudaMemsetAsync(g->status + ST_W_LO, 0, 7 * sizeof(uint64_t), s));
-    if (m > 0) {
-        int rc = reset_scan(g, 3, m, s);
-        if (rc) return rc;
-        // 16 records per thread (measured 15% faster than the 8 of the other
-        // scans); the flags reset above cover these fewer, larger tiles
-        constexpr int kItems = 16;
-        const int64_t tiles = (m + kScanBlock * kItems - 1) / (kScanBlock * kItems);
-        k_scan<U64x2, kScanBlock, kItems><<<(unsigned)tiles, kScanBlock, 0, s>>>(
-            m, scan_state<U64x2>(g, 3), U64x2{0, 0}, OpSum(), LoadWeights{g->rec},
-            StorePrefix{g->ptau, g->plam, g->status, m});
-        PS_LAUNCH_CHECK();
-    }
+    // the prefixes P_tau, P_lambda and their totals W, Lambda were written
+    // by the load step's edge-table kernel (with F_OVERFLOW if a sum passed
+    // 2^64); N_1 and the hub count are summed here
+    PS_CUDA_TRY(cudaMemsetAsync(g->status + ST_N1_LO, 0, 3 * sizeof(uint64_t), s));
     if (n > 0) {
         k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->tune.hub_min_degree, g->status);
         PS_LAUNCH_CHECK();

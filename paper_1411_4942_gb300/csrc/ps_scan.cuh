@@ -105,30 +105,34 @@ __device__ __forceinline__ U64x2 ld_cg<U64x2>(const U64x2 *p) {
     return U64x2{q[0], q[1]};
 }
 
-// Scans `count` items: item i = load(i); store(i, exclusive_i, inclusive_i).
 // A tile is BLOCK * ITEMS consecutive items; warp w owns the w-th run of
 // 32 * ITEMS of them and walks it in rows of 32 (lane-contiguous, so loads
-// and stores coalesce), scanning each row across the warp and carrying the
-// row total forward.
-template <typename T, int BLOCK, int ITEMS, typename Op, typename Load, typename Store>
-__global__ void __launch_bounds__(BLOCK)
-k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store) {
-    constexpr int NW = BLOCK / 32;
+// and stores coalesce): item wbase + 32 i of the calling lane is its i-th.
+// The tile id comes from a ticket (launch order), so a block only ever waits
+// on tiles already owned by running blocks.
+template <typename T>
+__device__ __forceinline__ int64_t scan_ticket(const ScanState<T> &st) {
     __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(st.counter, 1u);
+    __syncthreads();
+    return s_tile;
+}
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ int64_t scan_wbase(int64_t tile) {
+    return tile * (int64_t)(BLOCK * ITEMS) + (int64_t)(threadIdx.x >> 5) * (32 * ITEMS) + (threadIdx.x & 31);
+}
+
+// The scan of one tile whose items the block holds (v[i] = item
+// scan_wbase + 32 i, identity past `count`): each row scanned across the
+// warp with the row total carried forward, the warps' runs combined, the
+// tile's prefix found by look-back, then store(i, exclusive_i, inclusive_i).
+template <typename T, int BLOCK, int ITEMS, typename Op, typename Store>
+__device__ __forceinline__ void scan_tile(int64_t tile, int64_t wbase, T (&v)[ITEMS], int64_t count,
+                                          const ScanState<T> &st, T identity, Op op, Store store) {
+    constexpr int NW = BLOCK / 32;
     __shared__ T s_warp[NW];
     __shared__ T s_excl;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(st.counter, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t wbase = tile * (int64_t)(BLOCK * ITEMS) + (int64_t)warp * (32 * ITEMS) + lane;
-
-    T v[ITEMS];
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        const int64_t idx = wbase + 32 * i;
-        v[i] = idx < count ? load(idx) : identity;
-    }
     T carry = identity;
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
@@ -215,6 +219,50 @@ k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store
         const int64_t idx = wbase + 32 * i;
         if (idx < count) store(idx, op(run, prev), op(run, v[i]));
     }
+}
+
+// ------------------------------------------------ edge weights and prefixes
+
+// tau_j = (d_u - 1)(d_v - 1) (Section 3); lambda_j = L_{u,v} L_{v,u} with
+// L_{u,v} = d_u - 1 - iu, the neighbours of u after v in the order (Section 4).
+__device__ __forceinline__ U64x2 edge_weights(int32_t du, int32_t dv, int32_t iu, int32_t jv) {
+    const uint64_t t = static_cast<uint64_t>(du - 1) * static_cast<uint64_t>(dv - 1);
+    const uint64_t l = static_cast<uint64_t>(du - 1 - iu) * static_cast<uint64_t>(dv - 1 - jv);
+    return U64x2{t, l};
+}
+
+// The inclusive prefixes P_tau[j], P_lambda[j].  The weights are
+// non-negative, so a running sum that passes 2^64 shows up at the first item
+// whose inclusive prefix is below its exclusive one; the last item's
+// prefixes are W and Lambda.
+struct StorePrefix {
+    uint64_t *ptau, *plam;
+    u64 *status;
+    int64_t m;
+    __device__ void operator()(int64_t j, U64x2 exc, U64x2 inc) const {
+        ptau[j] = inc.a;
+        plam[j] = inc.b;
+        if (inc.a < exc.a || inc.b < exc.b) raise_flag(status, F_OVERFLOW);
+        if (j == m - 1) {
+            status[ST_W_LO] = inc.a;
+            status[ST_L_LO] = inc.b;
+        }
+    }
+};
+
+// Scans `count` items: item i = load(i); store(i, exclusive_i, inclusive_i).
+template <typename T, int BLOCK, int ITEMS, typename Op, typename Load, typename Store>
+__global__ void __launch_bounds__(BLOCK)
+k_scan(int64_t count, ScanState<T> st, T identity, Op op, Load load, Store store) {
+    const int64_t tile = scan_ticket(st);
+    const int64_t wbase = scan_wbase<BLOCK, ITEMS>(tile);
+    T v[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        const int64_t idx = wbase + 32 * i;
+        v[i] = idx < count ? load(idx) : identity;
+    }
+    scan_tile<T, BLOCK, ITEMS>(tile, wbase, v, count, st, identity, op, store);
 }
 
 }  // namespace ps
