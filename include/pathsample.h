@@ -100,7 +100,10 @@ typedef struct ps_graph ps_graph; /* opaque; host metadata + pointers into the w
 
 /* Bytes of device workspace a graph with n vertices and nnz stored arcs
  * (nnz = 2m) needs under tuning t (NULL = defaults).  0 if the sizes are
- * outside the supported range (n < 2^31, nnz < 2^31). */
+ * outside the supported range (n < 2^31, nnz < 2^31).  Test hook: a
+ * positive PS_TEST_ESET_LIST_CAP in the environment caps the hash set's
+ * per-region key lists (forcing its overflow and slow paths; results are
+ * unchanged); it must not change between this call and ps_load_csr. */
 size_t ps_graph_workspace_bytes(int64_t n, int64_t nnz, const ps_tuning *t);
 
 /* Section 2 input and Section 4 order.  Reads the CSR graph (d_off: int64
@@ -402,6 +405,19 @@ int ps_count_exact(const ps_graph *g, void *d_scratch, size_t scratch_bytes, ps_
 #define PS_PREFIX_STATIC_MAX_ITEMS (1ll << 27)
 int ps_prefix_pairs_static(const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_pa,
                            uint64_t *d_pb, int64_t count, ps_stream_t stream);
+
+/* ------------------------------------------------------- measurement aid */
+
+/* Not part of the method: reads the device buffer d_buf[0, bytes) `passes`
+ * times with loads cached in L2 only (ld.global.cg), each block its own
+ * even slice, and XORs a checksum into *d_sink (device, uint64) so the loads
+ * stay.  Timing the call with events on `stream` gives, for a buffer that
+ * fits in L2 (warm it with one pass first), the L2 read bandwidth that an
+ * L2-resident graph's samplers are reported against.  Asynchronous.
+ * PS_ERR_ARG when bytes is 0 or not a multiple of 16, d_buf is not 16-byte
+ * aligned, passes <= 0 or a pointer is missing. */
+int ps_l2_read_probe(const void *d_buf, uint64_t bytes, int32_t passes, uint64_t *d_sink,
+                     ps_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_NAME = "libpathsample.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
-SOURCES = ["ps_load.cu", "ps_prefix.cu", "ps_sample.cu", "ps_batch.cu", "ps_api.cu", "ps_static.cu", "ps_exact.cu", "ps_ingest.cu", "ps_order.cu", "ps_edges.cu"]
+SOURCES = ["ps_load.cu", "ps_prefix.cu", "ps_sample.cu", "ps_batch.cu", "ps_api.cu", "ps_static.cu", "ps_exact.cu", "ps_ingest.cu", "ps_order.cu", "ps_edges.cu", "ps_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

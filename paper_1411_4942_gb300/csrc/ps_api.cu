@@ -164,6 +164,12 @@ bool make_layout(int64_t n, int64_t nnz, const Tuning &t, Layout *L) {
     l.eset_cap = l.eset_regions ? (l.m_cap + l.eset_regions - 1) / l.eset_regions : 0;
     l.eset_cap += l.eset_cap / 8 + 64;
     l.eset_ov_cap = l.eset_regions ? 65536 + l.m_cap / 256 : 0;
+    // test hook: PS_TEST_ESET_LIST_CAP=c caps every region list at c keys, so
+    // the overflow list and, past it, the slow path take the other keys
+    if (const char *cap_env = std::getenv("PS_TEST_ESET_LIST_CAP")) {
+        const long long c = std::atoll(cap_env);
+        if (l.eset_regions && c > 0 && c < l.eset_cap) l.eset_cap = c;
+    }
     l.vtab_slots = t.adj_mode == kAdjVtab ? 2 * nnz : 0;
     l.radix_tiles = (n + kRadixTile - 1) / kRadixTile;
     if (l.radix_tiles < 1) l.radix_tiles = 1;

@@ -795,19 +795,18 @@ k_eset_upper(int64_t n, int64_t m, const int64_t *__restrict__ coff, const int32
 // (EsetLists); then one block per region inserts that region's keys with
 // shared-memory compare-and-swap, probing linearly within the region, and
 // writes the whole region out (empty slots included, so the table needs no
-// clearing).  A key whose probe runs past its region's end is left in the
-// list and inserted at the end by ordinary global compare-and-swap, probing
-// on into the following regions -- already written, so every bucket between
-// a key's home and its place is full, as a lookup assumes; so are the keys
-// of the overflow list.  The random read-modify-writes of the direct build
-// become sequential writes of the table plus the key lists' traffic.
+// clearing).  A key whose probe runs past its region's end goes to the
+// overflow list, and that list is inserted at the end by ordinary global
+// compare-and-swap, probing on into the following regions -- already
+// written, so every bucket between a key's home and its place is full, as a
+// lookup assumes.  The random read-modify-writes of the direct build become
+// sequential writes of the table plus the key lists' traffic.
 constexpr int kRegionThreads = 512;
 
 // One block per region (grid-stride): the region's keys into shared memory,
-// each placed key's list entry cleared to the empty marker, then the region
-// written out.
+// then the region written out.
 __global__ void __launch_bounds__(kRegionThreads)
-k_eset_regions(int64_t regions, int64_t region_buckets, EsetLists lists, uint64_t *set) {
+k_eset_regions(int64_t regions, int64_t region_buckets, EsetLists lists, uint64_t *set, u64 *status) {
     extern __shared__ unsigned long long s_tab[];
     const int64_t slots = region_buckets << kBucketShift;
     for (int64_t reg = blockIdx.x; reg < regions; reg += gridDim.x) {
@@ -831,7 +830,11 @@ k_eset_regions(int64_t regions, int64_t region_buckets, EsetLists lists, uint64_
                     }
                 }
             }
-            if (placed) list[e] = kEmptySlot;
+            if (!placed) {  // rare: every bucket from its home to the region's end is full
+                const uint32_t o = atomicAdd(lists.ov_count, 1u);
+                if (o < lists.ov_cap) lists.ov_keys[o] = key;
+                else status[ST_ESET_SPILL] = 1;
+            }
         }
         __syncthreads();
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(set) + (b0 << kBucketShift);
@@ -840,25 +843,15 @@ k_eset_regions(int64_t regions, int64_t region_buckets, EsetLists lists, uint64_
     }
 }
 
-// The keys whose probe ran past their region, and the overflow list's:
-// global compare-and-swap.
+// The overflow list (keys beyond their region list's capacity, and keys
+// whose probe ran past their region): global compare-and-swap.
 __global__ void __launch_bounds__(256)
-k_eset_leftovers(int64_t regions, EsetLists lists, uint64_t *set, u64 *status) {
-    const int64_t listed = regions * lists.cap;
+k_eset_leftovers(EsetLists lists, uint64_t *set, u64 *status) {
     const int64_t ov = *lists.ov_count < lists.ov_cap ? *lists.ov_count : lists.ov_cap;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     bool failed = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < listed + ov; e += stride) {
-        uint64_t key;
-        if (e < listed) {
-            const int64_t reg = e / lists.cap, i = e - reg * lists.cap;
-            if (i >= static_cast<int64_t>(lists.cur[reg])) continue;
-            key = lists.keys[e];
-        } else {
-            key = lists.ov_keys[e - listed];
-        }
-        if (key != kEmptySlot) failed |= !eset_insert(set, lists.mask, key);
-    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ov; e += stride)
+        failed |= !eset_insert(set, lists.mask, lists.ov_keys[e]);
     if (failed) raise_flag(status, F_OVERFLOW);
 }
 
@@ -1062,11 +1055,12 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
             const int smem = static_cast<int>(kRegionBuckets * kBucketSlots * sizeof(uint64_t));
             PS_CUDA_TRY(cudaFuncSetAttribute(k_eset_regions, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             const int64_t rb = regions < (int64_t)sms * 3 ? regions : (int64_t)sms * 3;
-            k_eset_regions<<<(unsigned)rb, kRegionThreads, smem, es>>>(regions, kRegionBuckets, lists, g->eset);
+            k_eset_regions<<<(unsigned)rb, kRegionThreads, smem, es>>>(regions, kRegionBuckets, lists, g->eset,
+                                                                       g->status);
             PS_LAUNCH_CHECK();
-            int64_t lb = (regions * L.eset_cap + 255) / 256;
-            if (lb > (int64_t)sms * 8) lb = (int64_t)sms * 8;
-            k_eset_leftovers<<<(unsigned)lb, 256, 0, es>>>(regions, lists, g->eset, g->status);
+            int64_t lb = (L.eset_ov_cap + 255) / 256;
+            if (lb > (int64_t)sms * 4) lb = (int64_t)sms * 4;
+            k_eset_leftovers<<<(unsigned)lb, 256, 0, es>>>(lists, g->eset, g->status);
             PS_LAUNCH_CHECK();
             k_eset_spill_fallback<<<(unsigned)eb, 256, 0, es>>>(n, m_cap, g->off, g->col, g->lowcnt, g->ubase,
                                                                g->eset, eset_mask, g->status);

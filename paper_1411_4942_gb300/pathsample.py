@@ -122,6 +122,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "ps_batch_sample_prepared": ([V, I32, V, I64, V, V, V, V], I32),
             "ps_kernel_launches": ([], U64),
             "ps_prefix_pairs_static": ([V, V, V, V, I64, V], I32),
+            "ps_l2_read_probe": ([V, U64, I32, V, V], I32),
             "ps_selftest_bounded_wait": ([V, ctypes.c_uint32, V], I32),
             "ps_exact_scratch_bytes": ([V, I32], SZ),
             "ps_ingest_workspace_bytes": ([I64, I64], SZ),
@@ -292,6 +293,13 @@ def ps_prefix_pairs_static(d_a, d_b, d_pa, d_pb, count: int, stream=None) -> int
     allocate device memory."""
     return int(load_library().ps_prefix_pairs_static(d_a, d_b, d_pa, d_pb, count,
                                                      _stream_ptr(stream)))
+
+
+def ps_l2_read_probe(d_buf, nbytes: int, passes: int, d_sink, stream=None) -> int:
+    """Measurement aid: reads a device buffer `passes` times with L2-only
+    loads (time it with events; for a buffer that fits in L2 this is the L2
+    read bandwidth)."""
+    return int(load_library().ps_l2_read_probe(d_buf, nbytes, passes, d_sink, _stream_ptr(stream)))
 
 
 def ps_exact_scratch_bytes(handle, max_blocks: int = 0) -> int:

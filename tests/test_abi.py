@@ -33,6 +33,17 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(ps.EXPORTED) <= declared
 
 
+def test_l2_probe_rejects_bad_arguments_before_any_cuda_call():
+    # dummy (never dereferenced) pointers: every case fails the argument checks
+    probe = ps.load_library().ps_l2_read_probe
+    assert probe(4096, 0, 1, 4096, None) == ps.PS_ERR_ARG       # no bytes
+    assert probe(4096, 24, 1, 4096, None) == ps.PS_ERR_ARG      # not a multiple of 16
+    assert probe(4104, 32, 1, 4096, None) == ps.PS_ERR_ARG      # buffer not 16-byte aligned
+    assert probe(4096, 32, 0, 4096, None) == ps.PS_ERR_ARG      # no passes
+    assert probe(None, 32, 1, 4096, None) == ps.PS_ERR_ARG
+    assert probe(4096, 32, 1, None, None) == ps.PS_ERR_ARG
+
+
 def test_built_for_sm_103a_only():
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -226,6 +226,22 @@ def test_tunings_do_not_change_results():
         assert h6.tolist() == ref6.tolist() and h4.tolist() == ref4.tolist()
 
 
+@pytest.mark.parametrize("n, d, cap", [(6000, 16.0, 8), (20000, 20.0, 1)])
+def test_hash_set_overflow_paths(monkeypatch, n, d, cap):
+    """The hash set's region lists capped at `cap` keys (a test hook): with
+    m ~ 48K the other keys all go to the overflow list; with m ~ 200K the
+    overflow list itself overflows and every edge is inserted again by the
+    slow path.  The adjacency answers, so the histograms, must not change."""
+    g = gg.chung_lu(n, d, 2.3, 8.0 * d, 17)
+    og = O.prepare(g.off, g.col)
+    monkeypatch.setenv("PS_TEST_ESET_LIST_CAP", str(cap))
+    G = _load(g)
+    monkeypatch.delenv("PS_TEST_ESET_LIST_CAP")
+    h6, h4 = _hists(G, 1 << 17, 1 << 17, 23)
+    assert h6.tolist() == O.sample_3paths(og, 1 << 17, 23, threads=8).tolist()
+    assert h4.tolist() == O.sample_centered(og, 1 << 17, 23, threads=8).tolist()
+
+
 def test_split_ranges_compose():
     g = gg.chung_lu(3000, 12.0, 2.3, 200.0, 2)
     G = _load(g)
