@@ -222,8 +222,9 @@ class Autotuner:
     real batch; caches the choice per device and graph-size bucket."""
 
     # hub-bitmap settings tried per graph-size bucket: (rows, smallest degree);
-    # rows -1 = none
-    HUB_CHOICES = ((-1, 0), (256, 64), (1024, 64), (1024, 16))
+    # rows -1 = none, (0, 0) = the library's defaults (up to 8192 rows within
+    # 48 bytes per edge, degree >= 64)
+    HUB_CHOICES = ((-1, 0), (0, 0), (1024, 64), (1024, 16), (4096, 16))
     # graph-size buckets by edges: below 2^17, below 2^20, the rest
     SIZE_EDGES = (1 << 17, 1 << 20)
     # smallest request taken in draw order (on graphs of >= ORDERED_MIN_EDGES)
