@@ -137,10 +137,10 @@ int ps_load_csr(int64_t n, int64_t nnz, const int64_t *d_off, const int32_t *d_c
  * the inclusive uint64 prefix sums that ps_load_csr wrote (exact, so the edge
  * draw is exact), computes N_1 of Alg. 2, the guide tables of the
  * inverse-CDF search and the structures of the chosen adjacency variant; no
- * sampler may run before it.  Synchronises `stream` once to
- * read the totals and fills *out; the guide tables and adjacency structures
- * are then finished in `stream` order, so sampling on another stream must
- * first wait for `stream`.  A second call returns the same totals without
+ * sampler may run before it.  Does not synchronise: the totals were read
+ * back by ps_load_csr, *out is filled at once, and the guide tables and
+ * adjacency structures are finished in `stream` order, so sampling on
+ * another stream must first wait for `stream`.  A second call returns the same totals without
  * recomputing.  Returns PS_NO_PATHS when W == 0 or Lambda == 0
  * (sampling then leaves histograms untouched), PS_ERR_OVERFLOW when a sum
  * does not fit in 64 bits, PS_ERR_TIMEOUT when a scan's bounded wait

@@ -49,6 +49,9 @@ struct Tuning {
     int draw_order;        // ordered samplers: 0 by size, 1 always, -1 never
 };
 Tuning resolve_tuning(const ps_tuning *t, int64_t n, int64_t nnz);
+// N_1 and the hub count into the status words (ps_prefix.cu); queued by the
+// load step once the degrees are known
+int launch_vertex_totals(ps_graph *g, cudaStream_t s);
 
 struct Layout {
     int64_t n, nnz, m_cap, gcap, hub_cap, hub_words, hub_bit_base, radix_tiles, scan_tiles;
@@ -86,6 +89,10 @@ struct ps_graph {
     uint64_t *eset;
     int32_t *vtab;
     bool prefixed;
+    // read back at the end of ps_load_csr: W, Lambda, N_1 (lo, hi), the hub
+    // count and the flags, so ps_tau_prefix needs no synchronisation
+    uint64_t load_totals[5] = {0, 0, 0, 0, 0};
+    uint64_t load_flags = 0;
     ps_stats stats;
     ps::GraphDev dev;
     // ev[0..2]: fork / join events of this graph's calls; ev[3]: end of the

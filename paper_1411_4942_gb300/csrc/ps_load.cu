@@ -1074,8 +1074,17 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
         PS_CUDA_TRY(cudaEventRecord(g->ev[3], es));
     }
 
+    // N_1 and the hub count (for ps_tau_prefix), read back with the flags
+    rc = launch_vertex_totals(g, s);
+    if (rc) return rc;
     PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
     PS_CUDA_TRY(cudaStreamSynchronize(s));
+    g->load_totals[0] = st[ST_W_LO];
+    g->load_totals[1] = st[ST_L_LO];
+    g->load_totals[2] = st[ST_N1_LO];
+    g->load_totals[3] = st[ST_N1_HI];
+    g->load_totals[4] = st[ST_HUBS];
+    g->load_flags = st[ST_FLAGS];
     const uint64_t m_upper = st[ST_M_UPPER];
     uint64_t flags = st[ST_FLAGS];
     if (2 * m_upper != static_cast<uint64_t>(nnz)) flags |= F_ASYM;

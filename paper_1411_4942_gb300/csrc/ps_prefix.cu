@@ -186,30 +186,31 @@ static int build_guide(ps_graph *g, const uint64_t *P, uint64_t total, int32_t *
     return PS_OK;
 }
 
+int launch_vertex_totals(ps_graph *g, cudaStream_t s) {
+    if (g->n <= 0) return PS_OK;
+    k_vertex_totals<<<g->sm_count * 8, 256, 0, s>>>(g->n, g->dnew, g->L.hub_cap, g->tune.hub_min_degree, g->status);
+    PS_LAUNCH_CHECK();
+    return PS_OK;
+}
+
 int prefix_graph(ps_graph *g, cudaStream_t s) {
     const int64_t n = g->n, m = g->m;
     const int sms = g->sm_count;
     // the prefixes P_tau, P_lambda and their totals W, Lambda were written
     // by the load step's edge-table kernel (with F_OVERFLOW if a sum passed
-    // 2^64); N_1 and the hub count are summed here
-    PS_CUDA_TRY(cudaMemsetAsync(g->status + ST_N1_LO, 0, 3 * sizeof(uint64_t), s));
-    if (n > 0) {
-        k_vertex_totals<<<sms * 8, 256, 0, s>>>(n, g->dnew, g->L.hub_cap, g->tune.hub_min_degree, g->status);
-        PS_LAUNCH_CHECK();
-    }
-    uint64_t st[ST_WORDS];
-    PS_CUDA_TRY(cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s));
-    PS_CUDA_TRY(cudaStreamSynchronize(s));
-    if (st[ST_FLAGS] & F_TIMEOUT) return PS_ERR_TIMEOUT;
+    // 2^64), N_1 and the hub count by its vertex pass; all were read back at
+    // its end
+    const uint64_t flags = g->load_flags;
+    if (flags & F_TIMEOUT) return PS_ERR_TIMEOUT;
     ps_stats &S = g->stats;
-    S.W = st[ST_W_LO];
-    S.Lambda = st[ST_L_LO];
-    S.N1_lo = st[ST_N1_LO];
-    S.N1_hi = st[ST_N1_HI];
+    S.W = g->load_totals[0];
+    S.Lambda = g->load_totals[1];
+    S.N1_lo = g->load_totals[2];
+    S.N1_hi = g->load_totals[3];
     S.n = n;
     S.m = m;
     S.d_max = g->d_max;
-    if (st[ST_FLAGS] & F_OVERFLOW) return PS_ERR_OVERFLOW;
+    if (flags & F_OVERFLOW) return PS_ERR_OVERFLOW;
 
     // guide tables (with guides off the table has at most 2 buckets)
     int tshift = 0, lshift = 0;
@@ -240,7 +241,7 @@ int prefix_graph(ps_graph *g, cudaStream_t s) {
     }
 
     // hub bitmaps
-    const int64_t hubs = static_cast<int64_t>(st[ST_HUBS]);
+    const int64_t hubs = static_cast<int64_t>(g->load_totals[4]);
     S.hubs = hubs;
     if (hubs > 0) {
         const int64_t words = g->L.hub_words;
