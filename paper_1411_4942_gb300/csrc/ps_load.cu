@@ -397,18 +397,131 @@ __device__ __forceinline__ void sort_row_block(const RowIn &R, int64_t r, uint32
     __syncthreads();  // s_low and smem are free for the next row
 }
 
+// Bucket of label x for the bucketed row sort: 256 buckets in label order,
+// fine near the top labels and coarse far from them -- a float-like code
+// (exponent and three mantissa bits) of the distance n - 1 - x from the
+// top.  In degree order a long row's neighbours crowd the top labels (their
+// density falls roughly as a power of that distance), which this spreads
+// evenly: on the 3M-vertex graph a 1025..4096-entry row's largest bucket
+// holds at most ~100 entries, against ~900 for the top 8 label bits.
+__device__ __forceinline__ int row_bucket(int32_t x, int32_t top) {
+    const uint32_t y1 = static_cast<uint32_t>(top - x) + 1u;  // 1 .. n
+    const int e = 31 - __clz(y1);
+    const uint32_t m = e >= 3 ? (y1 >> (e - 3)) & 7u : (y1 << (3 - e)) & 7u;
+    return 255 - (e * 8 + static_cast<int>(m));
+}
+
+// One warp sorts the run p[0, s) of shared memory (s <= 32 E).
+template <int E>
+__device__ __forceinline__ void sort_run_warp(int32_t *p, int s) {
+    const int lane = threadIdx.x & 31;
+    int32_t x[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = lane * E + i;
+        x[i] = idx < s ? p[idx] : INT_MAX;
+    }
+    bitonic_blocked<E, 32>(x, nullptr);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+        const int idx = lane * E + i;
+        if (idx < s) p[idx] = x[i];
+    }
+}
+
+// Tier C by buckets: the row relabelled into shared memory, counted and
+// scattered into its 256 buckets (row_bucket), each bucket sorted by one
+// warp, the row written out.  A row with a bucket above 256 entries (none on
+// the benchmark graphs) takes the block-wide bitonic sort above instead.
+constexpr int kBucketRun = 256;
+
 __global__ void __launch_bounds__(512, 3) k_sort_tier_c(RowIn R) {
-    extern __shared__ int32_t s_dyn[];
-    __shared__ int s_low;
+    __shared__ int32_t s_a[kTierC];
+    __shared__ int32_t s_b[kTierC];
+    __shared__ uint32_t s_cnt[256], s_start[257];
+    __shared__ int s_low, s_big;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t r0 = static_cast<int64_t>(R.status[ST_TIER + 2]);
     const int64_t r1 = static_cast<int64_t>(R.status[ST_TIER + 3]);
+    const int32_t top = static_cast<int32_t>(R.n - 1);
     bool bad = false, nsimple = false;
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const uint32_t v = R.inv[r];
         const int64_t o = ldg_i64(R.off + v);
         const int d = static_cast<int>(ldg_i64(R.off + v + 1) - o);
-        if (d <= 2048) sort_row_block<4>(R, r, v, o, d, s_dyn, &s_low, bad, nsimple);
-        else sort_row_block<8>(R, r, v, o, d, s_dyn, &s_low, bad, nsimple);
+        if (t < 256) s_cnt[t] = 0;
+        if (t == 0) {
+            s_low = 0;
+            s_big = 0;
+        }
+        __syncthreads();
+        for (int i = t; i < d; i += 512) {
+            const int32_t x = relabel(R, o + i, v, static_cast<int32_t>(r), bad, nsimple);
+            s_a[i] = x;
+            atomicAdd(&s_cnt[row_bucket(x, top)], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan of the 256 counts, 8 per lane
+            uint32_t c[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                c[j] = s_cnt[lane * 8 + j];
+                sum += c[j];
+                if (c[j] > kBucketRun) s_big = 1;
+            }
+            uint32_t x = sum;
+#pragma unroll
+            for (int off2 = 1; off2 < 32; off2 <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, off2);
+                if (lane >= off2) x += y;
+            }
+            uint32_t run = x - sum;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                s_start[lane * 8 + j] = run;
+                s_cnt[lane * 8 + j] = run;  // becomes the scatter cursor
+                run += c[j];
+            }
+            if (lane == 31) s_start[256] = run;
+        }
+        __syncthreads();
+        if (s_big) {
+            // every thread reads s_big after the barrier, so the branch is uniform
+            __syncthreads();
+            sort_row_block<8>(R, r, v, o, d, s_b, &s_low, bad, nsimple);
+            continue;
+        }
+        for (int i = t; i < d; i += 512) {
+            const int32_t x = s_a[i];
+            s_b[atomicAdd(&s_cnt[row_bucket(x, top)], 1u)] = x;
+        }
+        __syncthreads();
+        for (int b = warp; b < 256; b += 16) {
+            const int st = static_cast<int>(s_start[b]);
+            const int sz = static_cast<int>(s_start[b + 1]) - st;
+            if (sz <= 1) continue;
+            if (sz <= 32) sort_run_warp<1>(s_b + st, sz);
+            else if (sz <= 64) sort_run_warp<2>(s_b + st, sz);
+            else if (sz <= 128) sort_run_warp<4>(s_b + st, sz);
+            else sort_run_warp<8>(s_b + st, sz);
+        }
+        __syncthreads();
+        int32_t *dst = R.ccol + R.coff[r];
+        int low = 0;
+        for (int i = t; i < d; i += 512) {
+            const int32_t x = s_b[i];
+            dst[i] = x;
+            low += x < static_cast<int32_t>(r);
+            if (i + 1 < d && s_b[i + 1] == x) nsimple = true;
+        }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) low += __shfl_down_sync(0xffffffffu, low, o2);
+        if (lane == 0) atomicAdd(&s_low, low);
+        __syncthreads();
+        if (t == 0) R.lowcnt[r] = s_low;
+        __syncthreads();  // the shared arrays are free for the next row
     }
     report(R, bad, nsimple);
 }
@@ -991,8 +1104,7 @@ int load_graph(ps_graph *g, const int64_t *d_off, const int32_t *d_col, cudaStre
             PS_LAUNCH_CHECK();
         }
         if (g->d_max > kTierB) {
-            const int smem = kTierC * (int)sizeof(int32_t);
-            k_sort_tier_c<<<sms * 4, 512, smem, fork.side(0)>>>(R);
+            k_sort_tier_c<<<sms * 3, 512, 0, fork.side(0)>>>(R);
             PS_LAUNCH_CHECK();
         }
         k_sort_tier_b<<<sms * 8, 256, 0, s>>>(R);

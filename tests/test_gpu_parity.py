@@ -201,6 +201,26 @@ def test_long_rows_use_every_sort_tier():
     assert h4.tolist() == O.sample_centered(og, 200003, 5, threads=8).tolist()
 
 
+def test_bucketed_row_sort_and_its_fallback():
+    """Rows of 1025..4096 entries are sorted through 256 label buckets; a row
+    whose entries crowd one bucket (here a vertex joined to 1,500 leaves,
+    which take the lowest labels) takes the block-wide bitonic sort."""
+    n = 20000
+    rs = np.random.Generator(np.random.PCG64(41))
+    pairs = [(0, i) for i in range(1, 1501)]
+    others = np.arange(1502, n)
+    pairs += [(1501, int(x)) for x in rs.choice(others, 3000, replace=False)]
+    pairs += [(1502, int(x)) for x in rs.choice(others[1:], 1100, replace=False)]
+    a = rs.integers(1502, n, size=60000)
+    b = rs.integers(1502, n, size=60000)
+    pairs += list(zip(a.tolist(), b.tolist()))
+    g = gg.relabel(gg.from_pairs(n, pairs), rs.permutation(n))
+    og, G = _check_structure(g)
+    h6, h4 = _hists(G, 200003, 200003, 8)
+    assert h6.tolist() == O.sample_3paths(og, 200003, 8, threads=8).tolist()
+    assert h4.tolist() == O.sample_centered(og, 200003, 8, threads=8).tolist()
+
+
 def test_tunings_do_not_change_results():
     g = gg.chung_lu(20000, 15.0, 2.1, 1500.0, 12)
     og = O.prepare(g.off, g.col)
