@@ -221,6 +221,30 @@ def test_bucketed_row_sort_and_its_fallback():
     assert h4.tolist() == O.sample_centered(og, 200003, 8, threads=8).tolist()
 
 
+def test_long_rows_past_2_20_labels():
+    """Over 2^20 vertices (past the shared-memory bitmap's one chunk), rows
+    above 4096 entries take the block radix sort: a row of 6000 spread
+    entries, one of 5000 leaves, which are the only degree-1 vertices and so
+    hold consecutive labels, and one of 20000 entries.  The other neighbours
+    form a cycle with chords, so no other vertex has degree 1."""
+    n = 1_100_000
+    rs = np.random.Generator(np.random.PCG64(77))
+    core = np.arange(30000, 130000)
+    cyc = rs.permutation(core)
+    pairs = list(zip(cyc.tolist(), np.roll(cyc, 1).tolist()))
+    a = rs.choice(core, 100000)
+    b = rs.choice(core, 100000)
+    pairs += list(zip(a.tolist(), b.tolist()))
+    pairs += [(0, int(x)) for x in rs.choice(core, 6000, replace=False)]
+    pairs += [(1, i) for i in range(10, 5010)]
+    pairs += [(2, int(x)) for x in rs.choice(core, 20000, replace=False)]
+    g = gg.relabel(gg.from_pairs(n, pairs), rs.permutation(n))
+    og, G = _check_structure(g)
+    h6, h4 = _hists(G, 1 << 18, 1 << 18, 9)
+    assert h6.tolist() == O.sample_3paths(og, 1 << 18, 9, threads=8).tolist()
+    assert h4.tolist() == O.sample_centered(og, 1 << 18, 9, threads=8).tolist()
+
+
 def test_tunings_do_not_change_results():
     g = gg.chung_lu(20000, 15.0, 2.1, 1500.0, 12)
     og = O.prepare(g.off, g.col)
