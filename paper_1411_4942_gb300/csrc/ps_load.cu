@@ -797,11 +797,9 @@ __device__ __forceinline__ bool eset_insert(uint64_t *set, uint64_t mask, uint64
 // compare-and-swaps are issued together (most succeed at once), and only
 // the keys whose first slot was taken go on to the full insertion.
 constexpr int kInsertBatch = 4;
-#ifndef PS_ESET_BLOCKS
-#define PS_ESET_BLOCKS 8
-#endif
-// resident blocks per SM of the hash set build beside the edge table
-constexpr int kEsetBlocksPerSm = PS_ESET_BLOCKS;
+// resident blocks per SM of the direct hash set build (4, 8 and 16 measured
+// the same)
+constexpr int kEsetBlocksPerSm = 8;
 
 __device__ __forceinline__ bool eset_insert_batch(uint64_t *set, uint64_t mask, const uint64_t (&key)[kInsertBatch],
                                                   const bool (&ok)[kInsertBatch]) {
