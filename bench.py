@@ -237,9 +237,14 @@ REFERENCE_SLICE = (1 << 22, 1 << 21)
 
 
 def _oracle_worker(conn, off, col, seed, slices):
-    """The oracle in its own process: its prepare (validation, relabelling,
-    edge table and prefixes) at once, so it overlaps the GPU arm's set-up;
-    then, on request, the bounded sampling slices, timed."""
+    """The oracle in its own process: on request its prepare (validation,
+    relabelling, edge table and prefixes), then the bounded sampling slices,
+    timed.  It waits until the GPU arm's timed legs are over: running beside
+    them, its 16 threads took the host cores and host memory bandwidth that
+    the end-to-end leg's upload and launches need (36.3 against 33.0 ms per
+    step on the 3M-vertex graph)."""
+    if conn.recv() != "prepare":
+        return
     sys.path.insert(0, ROOT)
     import oracle as O
     t0 = time.perf_counter()
@@ -270,7 +275,7 @@ def _oracle_worker(conn, off, col, seed, slices):
 class OracleLeg:
     """The CPU baseline of the benchmark line: the oracle as it stands, on the
     host cores, on bounded slices of the same workload.  Started (spawned)
-    before the GPU arm touches CUDA; its slices run after the timed region."""
+    before the GPU arm touches CUDA; it works only after the timed legs."""
 
     def __init__(self, g, seed, slices, k3, kc):
         import multiprocessing as mp
@@ -281,10 +286,21 @@ class OracleLeg:
                                 daemon=True)
         self.proc.start()
 
+    def _recv(self, limit_s=1800.0):
+        # never wait on a worker that has died (a spawn or import failure)
+        t0 = time.perf_counter()
+        while not self.conn.poll(1.0):
+            if not self.proc.is_alive():
+                raise RuntimeError("the oracle leg's process ended before replying")
+            if time.perf_counter() - t0 > limit_s:
+                raise TimeoutError("the oracle leg did not reply in time")
+        return self.conn.recv()
+
     def run(self):
-        ready = self.conn.recv()
+        self.conn.send("prepare")
+        ready = self._recv()
         self.conn.send("go")
-        res = self.conn.recv()
+        res = self._recv()
         res.update({k: ready[k] for k in ("W", "Lambda", "N1")})
         self.proc.join(timeout=60)
         return res
