@@ -177,11 +177,16 @@ k_esort_hist(int64_t count, const uint32_t *__restrict__ key, int shift, uint32_
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortBlock) (&s_h[0][0])[d] = 0u;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortItems) + lane;
-#pragma unroll 4
+    // all of a thread's keys in flight at once, then the counts
+    uint32_t k[kSortItems];
+#pragma unroll
     for (int q = 0; q < kSortItems; q++) {
         const int64_t idx = base + 32 * q;
-        if (idx < count) atomicAdd(&s_h[warp][(__ldg(key + idx) >> shift) & 255u], 1u);
+        k[q] = idx < count ? __ldg(key + idx) : 0u;
     }
+#pragma unroll
+    for (int q = 0; q < kSortItems; q++)
+        if (base + 32 * q < count) atomicAdd(&s_h[warp][(k[q] >> shift) & 255u], 1u);
     __syncthreads();
     uint32_t c = 0;
 #pragma unroll
